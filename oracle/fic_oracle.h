@@ -1,0 +1,134 @@
+/*
+ * fic_oracle.h -- plain, slow CPU oracle of the fractal encoder's matching
+ * search (test infrastructure only).
+ *
+ * Only the tests, the package's smoke check and the benchmark's CPU-baseline
+ * leg may call this library.  It shares no code with the CUDA path.
+ *
+ * Everything follows "A Fast Fractal Image Compression Algorithm Using
+ * Predefined Values for Contrast Scaling" (Miar Naimi, Salarian):
+ *   Sec. 2     range partition, domain pool (2B x 2B squares at step L),
+ *              the 8 isometries, the distance of Eq. 1, s and o of Eq. 2-3,
+ *              the quadtree split 16 -> 8 -> 4 -> 2.
+ *   Sec. 3     block entropy (Eq. 4-5) and the "entropy greater than a
+ *              threshold" pool filter.
+ *   Sec. 3.1   the predefined contrast-scaling sets per step.
+ * Readings of points the paper leaves open are stated beside each function.
+ */
+#ifndef FIC_ORACLE_H
+#define FIC_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* S-set selection. */
+#define ORACLE_S_PREDEFINED 0 /* Sec. 3.1 per-step sets, denominators 10  */
+#define ORACLE_S_GRID 1       /* k/(M-1), k = 0..M-1 (Sec. 2 "pre-sampled") */
+
+typedef struct {
+  int n_levels;              /* 1..4 */
+  int range_size0;           /* B at the first level: 16, 8, 4 or 2      */
+  int domain_step;           /* L >= 1                                    */
+  double rms_threshold;      /* accept when E <= n * T^2                  */
+  int single_level;          /* 1: accept every range at the first level  */
+  int s_mode;                /* ORACLE_S_PREDEFINED | ORACLE_S_GRID       */
+  int grid_samples;          /* M for ORACLE_S_GRID                       */
+  double entropy_percentile; /* 0 <= p <= 1                               */
+  int n_threads;             /* OpenMP threads for the range loop (>= 1)  */
+} oracle_params;
+
+/* One saved affine transformation (Sec. 2). */
+typedef struct {
+  int32_t level, x, y, size;   /* range block: top-left corner, side B    */
+  int32_t dom_index;           /* raster index in the unfiltered pool     */
+  int32_t dom_x, dom_y;        /* domain block top-left corner (2B x 2B)  */
+  int32_t iso;                 /* isometry 0..7                           */
+  int32_t s_idx, p, q;         /* s = p / q, s_idx its index in the set   */
+  int32_t pad;
+  int64_t e_num;               /* 16 q^2 n^2 E, exact                     */
+  int64_t o_num;               /* 4 q n o, exact                          */
+  double e;                    /* E = e_num / (16 q^2 n^2)                */
+  double s;                    /* p / q                                   */
+  double o;                    /* o_num / (4 q n)                         */
+} oracle_code;
+
+typedef struct {
+  int64_t e_num;               /* 16 q^2 n^2 E of the best candidate      */
+  int64_t key;                 /* (dom_index * 8 + iso) * |S| + s_idx     */
+  int32_t dom_index, iso, s_idx, pad;
+} oracle_match_result;
+
+typedef struct {
+  int32_t size;                /* B                                       */
+  int32_t pool_size;           /* P                                       */
+  int32_t n_kept;
+  int32_t fallback;            /* 1 when the strict filter kept nothing   */
+  int64_t thr_key;
+  int32_t n_active;            /* ranges matched at this level            */
+  int32_t n_accepted;
+  double matches;              /* n_active * n_kept * 8                   */
+} oracle_level_stats;
+
+/* Eq. 4-5: entropy (natural log) of the size x size block at (x, y). */
+double oracle_entropy(const uint8_t* img, long pitch, int x, int y, int size);
+
+/* Fixed-point entropy key of the same block: sum over grey levels of
+ * round(q ln q * 2^32), q the level's count.  H = ln(N) - key / (N 2^32), so
+ * a larger key means a lower entropy. */
+int64_t oracle_entropy_key(const uint8_t* img, long pitch, int x, int y, int size);
+
+/* table[q] = round(q ln q * 2^32), q = 0..qmax. */
+void oracle_key_table(int64_t* table, int qmax);
+
+/* Number of pool positions for block size B and step L (Sec. 2). */
+int oracle_pool_size(int W, int H, int B, int L, int* px, int* py);
+
+/* Entropy keys of every pool position (raster order), the percentile
+ * threshold and the kept list (ascending raster index).  Returns n_kept. */
+int oracle_pool_filter(const uint8_t* img, long pitch, int W, int H, int B, int L,
+                       double percentile, int64_t* keys, int32_t* kept,
+                       int64_t* thr_key, int* fallback);
+
+/* 2x2 sums of the 2B x 2B block at (x, y): Ds[i*B+j] (Eq. 1's decimated
+ * block is Ds / 4). */
+void oracle_decimate(const uint8_t* img, long pitch, int x, int y, int B, int64_t* Ds);
+
+/* dst = T_k(src) for a B x B block, k = 0..7 (Sec. 2). */
+void oracle_isometry(const int64_t* src, int B, int k, int64_t* dst);
+
+/* 16 q^2 n^2 E(R, D) of Eq. 1 with s = p/q and o from Eq. 3, computed term
+ * by term in exact integers.  R: range pixels; D: decimated sums Ds (already
+ * transformed); n = B*B. */
+int64_t oracle_error_num(const int64_t* R, const int64_t* Ds, int n, int p, int q);
+
+/* Eq. 1 evaluated in long double with s = p/q and o = Rbar - s Dbar. */
+double oracle_error_direct(const int64_t* R, const int64_t* Ds, int n, int p, int q);
+
+/* S set of a level: fills p[] and *q, returns |S|. */
+int oracle_s_set(int s_mode, int grid_samples, int B, int32_t* p, int32_t* q);
+
+/* Best (domain, isometry, s) for each listed range (x, y at size B) against
+ * the kept pool, exhaustive over the definition (Sec. 2). */
+void oracle_match(const uint8_t* img, long pitch, int W, int H, int B, int L,
+                  const int32_t* kept, int n_kept, const int32_t* range_xy,
+                  int n_ranges, const int32_t* s_p, int n_s, int q, int n_threads,
+                  oracle_match_result* out);
+
+/* Full quadtree encoder.  Returns the number of codes (or -1 if cap is too
+ * small, -2 on bad arguments).  stats has n_levels entries. */
+int oracle_encode(const uint8_t* img, long pitch, int W, int H, const oracle_params* prm,
+                  oracle_code* codes, int cap, oracle_level_stats* stats);
+
+/* Fixed-point decoder: Jacobi iteration from a flat 128 image, stopping
+ * when max |delta| < tol or after max_iters.  out: W*H doubles.  Returns the
+ * number of iterations done. */
+int oracle_decode(const oracle_code* codes, int n_codes, int W, int H, int max_iters,
+                  double tol, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
