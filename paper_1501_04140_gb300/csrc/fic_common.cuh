@@ -1,0 +1,113 @@
+// fic_common.cuh -- shared definitions of the CUDA encoder (sm_103a).
+//
+// Notation follows "A Fast Fractal Image Compression Algorithm Using
+// Predefined Values for Contrast Scaling" (Miar Naimi, Salarian): B is the
+// range side (16 -> 8 -> 4 -> 2, Sec. 2), n = B*B, L the domain step, a domain
+// is a 2B x 2B square decimated to B x B (Eq. 1), s = p/q the contrast scale
+// and o the offset of Eq. 3.  All integer moments are exact; the decimated
+// block is carried as the integer 2x2 sum Ds (the paper's D is Ds / 4).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fic.h"
+
+namespace fic {
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxImages = 4096;      // images per fic_encode call
+constexpr int kMaxS = 32;             // |S| of a level
+constexpr int kKeyTableN = 1024;      // 4 B^2 for B = 16: pixels of a domain
+constexpr int kTileRanges = 16;       // ranges per M tile (x 8 isometries = 128 rows)
+constexpr int kTileRows = 128;        // M of the tensor tile
+constexpr int kTileDoms = 128;        // N of one domain tile
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // bounded mbarrier waits: 2 s
+
+// device status word bits (ctx->d_status)
+constexpr uint32_t kStatusTimeout = 1u;
+constexpr uint32_t kStatusOverflow = 2u;
+
+// ---------------------------------------------------------------- images
+struct ImgDev {
+  const uint8_t* pix;  // device pointer, row-major
+  int W, H, pitch;
+  int px, py;          // pool positions per row / column at the level
+};
+
+// Active range of a level: image, top-left corner.
+struct RangeRec {
+  int32_t img, x, y, parent;  // parent: index in the previous level (-1 at level 0)
+};
+
+// Per-range moments used by the scoring epilogues.
+struct RangeMom {
+  int32_t sr;      // sum of r
+  int32_t srp;     // sum of (r - 128)
+  int64_t a;       // n sum r^2 - (sum r)^2
+};
+
+// Per kept domain, for the scoring epilogues.
+struct DomRec {
+  int64_t v;       // n sum Ds^2 - (sum Ds)^2  (= 16 n^2 Var(D) scaled, shift invariant)
+  int32_t sdp;     // sum of (Ds - 512)
+  int32_t pos;     // raster index in the unfiltered pool of its image
+};
+
+// Level-wide constants of the S set (Sec. 2 grid or Sec. 3.1 values).
+struct SSet {
+  int m;            // |S|
+  int q;            // common denominator
+  int grid;         // 1: grid k/(M-1) (convex shortcut), 0: explicit list
+  int p[kMaxS];     // numerators
+};
+
+// Exact lexicographic candidate: score first, then the tie-break key.
+struct Cand {
+  int64_t score;    // E' (exact, tensor path) or float bits (fp32 path)
+  int64_t key;      // (pos * 8 + iso) * |S| + s_idx
+};
+
+// ---------------------------------------------------------------- helpers
+__host__ __device__ inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Upper bound (exclusive) search: index i with off[i] <= x < off[i+1].
+__device__ inline int find_segment(const int64_t* off, int n, int64_t x) {
+  int lo = 0, hi = n;  // off[0] = 0 <= x < off[n]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (off[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Isometry k of Sec. 2 as a map of block coordinates: output pixel (i, j) of
+// T_k(D) is taken from D at iso_src(k, i, j).  k = 0..3 turns the block
+// clockwise by 90k degrees, k = 4..7 mirrors left-right after turning by
+// 90(k-4) degrees.
+__host__ __device__ inline void iso_src(int B, int k, int i, int j, int* si, int* sj) {
+  const int m = B - 1;
+  int jj = (k & 4) ? m - j : j;       // mirror acts on the turned block
+  switch (k & 3) {
+    case 0: *si = i;      *sj = jj;     break;
+    case 1: *si = m - jj; *sj = i;      break;  // top row -> right column
+    case 2: *si = m - i;  *sj = m - jj; break;
+    default: *si = jj;    *sj = m - i;  break;  // top row -> left column
+  }
+}
+
+}  // namespace fic
+
+#define FIC_CUDA_TRY(expr)                                   \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) return ::fic::cuda_status(_e);    \
+  } while (0)
+
+namespace fic {
+inline int cuda_status(cudaError_t e) {
+  return e == cudaErrorMemoryAllocation ? FIC_ENOMEM : FIC_ECUDA;
+}
+}  // namespace fic

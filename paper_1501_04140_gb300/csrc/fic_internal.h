@@ -1,0 +1,64 @@
+// fic_internal.h -- host-side structures and launchers shared by the
+// translation units of the CUDA encoder (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "fic_common.cuh"
+
+namespace fic {
+
+// Device buffer owned by a plan; grows, never shrinks.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int reserve(size_t want);
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Selection state of one image's pool (exact percentile by radix select).
+struct SelState {
+  int64_t prefix;   // key bits chosen so far
+  int64_t rank;     // rank still to find inside the current prefix
+  int64_t nlt;      // keys strictly below the prefix region
+  int64_t nle;      // after the last pass: keys <= threshold
+  int64_t thr;      // threshold key (after the last pass)
+  int32_t nkept;    // kept domains
+  int32_t fallback; // 1: nothing had key < thr, kept key <= thr
+  int64_t base;     // sum of nkept of the images before this one
+};
+
+constexpr int kSelBits = 9;
+constexpr int kSelBins = 1 << kSelBits;
+constexpr int kSelPasses = 5;  // 45 key bits: keys are below 1024 ln(1024) 2^32 < 2^45
+
+// Entropy-filtered domain pool of one level over a batch of images.
+struct PoolLevel {
+  int B = 0, L = 0, n = 0, Kp = 0, n_images = 0;
+  int64_t P_tot = 0;                 // pool positions over all images
+  int64_t S_tot = 0;                 // domain slots (each image's rounded up to 128)
+  std::vector<int64_t> h_off;        // n_images + 1 position offsets
+  std::vector<int64_t> h_slot_off;   // n_images + 1 slot offsets (multiples of 128)
+  std::vector<ImgDev> h_img;         // with px, py of this level
+  bool want_tc = false, want_f32 = false;
+  SSet sset{};
+  double pct = 0.5;                  // entropy percentile of the threshold
+  int nsm = 0;                       // SMs of the device (grid sizing)
+  // per position: off, keys, sd, sq; per slot: slot_off, kept, bpack, b32, dom, domf
+  DevBuf off, slot_off, img, keys, sd, sq, sel, hist, kept, bpack, b32, dom, domf, scan_scratch,
+      total;
+};
+
+// Launchers (pool.cu)
+int pool_build(PoolLevel& pl, const int64_t* d_dT, cudaStream_t st);
+void make_sset(int s_mode, int grid_samples, int B, SSet* out);
+int host_key_table(int64_t* dT, int nmax);
+
+// scan.cu
+__global__ void k_scan_blocks(int32_t* cnt, int nb, int64_t* total);
+
+}  // namespace fic

@@ -1,0 +1,315 @@
+// level.cu -- per-level steps around the matcher (Sec. 2):
+//   k_range_pack     active ranges -> exact moments and the 8 isometric copies
+//                    T_k^-1(R) as matcher rows (f16 r - 128 and/or fp32);
+//   k_plan           work items (image, 16-range M tile, chunk of 128-domain
+//                    tiles) over a batch, from device-side counts;
+//   k_reduce_final   best candidate of every range over its 8 isometry rows
+//                    and all domain chunks, then Eq. 1 and Eq. 3 in exact
+//                    integers for the chosen map;
+//   k_split_*        accept when E <= n T^2 (last level: always), otherwise
+//                    split into four children (16 -> 8 -> 4 -> 2).
+#include <math.h>
+
+#include "fic_internal.h"
+#include "level.cuh"
+#include "scan.cuh"
+
+namespace fic {
+
+__global__ void __launch_bounds__(1024) k_scan_blocks(int32_t* cnt, int nb, int64_t* total) {
+  __shared__ int sw[32];
+  __shared__ int tot;
+  int64_t carry = 0;
+  for (int base = 0; base < nb; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? cnt[i] : 0;
+    const int before = block_excl_scan(v, sw, &tot);
+    if (i < nb) cnt[i] = (int32_t)(carry + before);
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+// ---------------------------------------------------------------- range operand
+template <int B>
+__global__ void k_range_pack(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec,
+                             const int64_t* __restrict__ n_act, int Kp,
+                             RangeMom* __restrict__ mom, uint16_t* __restrict__ apack,
+                             float* __restrict__ a32) {
+  constexpr int n = B * B;
+  const int64_t N = *n_act;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const RangeRec r = rec[g];
+    const ImgDev I = imgs[r.img];
+    const uint8_t* base = I.pix + (int64_t)r.y * I.pitch + r.x;
+    int sr = 0;
+    int64_t s2 = 0;
+    for (int i = 0; i < B; ++i)
+      for (int j = 0; j < B; ++j) {
+        const int v = base[(int64_t)i * I.pitch + j];
+        sr += v;
+        s2 += v * v;
+        // row k holds T_k^-1(R): <T_k^-1 R, D> = <R, T_k D>
+        for (int k = 0; k < 8; ++k) {
+          int si, sj;
+          iso_src(B, k, i, j, &si, &sj);
+          const int e = si * B + sj;
+          if (apack) {
+            const int64_t idx = (((g * (Kp >> 3)) + (e >> 3)) * 8 + k) * 8 + (e & 7);
+            apack[idx] = __half_as_ushort(__int2half_rn(v - 128));
+          }
+          if (a32) a32[(g * 8 + k) * n + e] = (float)(v - 128);
+        }
+      }
+    if (apack && n < Kp)
+      for (int e = n; e < Kp; ++e)
+        for (int k = 0; k < 8; ++k) apack[(((g * (Kp >> 3)) + (e >> 3)) * 8 + k) * 8 + (e & 7)] = 0;
+    RangeMom m;
+    m.sr = sr;
+    m.srp = sr - 128 * n;
+    m.a = (int64_t)n * s2 - (int64_t)sr * sr;
+    mom[g] = m;
+  }
+}
+
+int launch_range_pack(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
+                      int64_t cap, int Kp, RangeMom* mom, uint16_t* apack, float* a32,
+                      cudaStream_t st) {
+  const int threads = 128;
+  int grid = (int)ceil_div64(cap > 0 ? cap : 1, threads);
+  if (grid > 65535) grid = 65535;
+  switch (B) {
+    case 16: k_range_pack<16><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, apack, a32); break;
+    case 8: k_range_pack<8><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, apack, a32); break;
+    case 4: k_range_pack<4><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, apack, a32); break;
+    case 2: k_range_pack<2><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, apack, a32); break;
+    default: return FIC_EINVAL;
+  }
+  return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
+}
+
+// ---------------------------------------------------------------- plan
+// One thread: images are few (<= kMaxImages) and this runs once per level.
+__global__ void k_plan(int n_images, const int64_t* __restrict__ act_off,
+                       const int64_t* __restrict__ act_cnt, const SelState* __restrict__ sel,
+                       int target_items, int64_t item_cap, int64_t mt_cap, PlanMeta* meta,
+                       int64_t* __restrict__ item_off, int32_t* __restrict__ chunks) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t work = 0;
+  for (int i = 0; i < n_images; ++i)
+    work += ceil_div64(act_cnt[i], kTileRanges) * ceil_div64(sel[i].nkept, kTileDoms);
+  int64_t ch = ceil_div64(work, target_items > 0 ? target_items : 1);
+  if (ch < 1) ch = 1;
+  const int64_t room = item_cap - mt_cap;
+  if (room > 0) {
+    const int64_t need = ceil_div64(work, room);
+    if (ch < need) ch = need;
+  }
+  int64_t items = 0;
+  for (int i = 0; i < n_images; ++i) {
+    const int64_t mt = ceil_div64(act_cnt[i], kTileRanges);
+    const int64_t nt = ceil_div64(sel[i].nkept, kTileDoms);
+    const int64_t c = nt > 0 ? ceil_div64(nt, ch) : 0;
+    item_off[i] = items;
+    chunks[i] = (int32_t)c;
+    items += mt * c;
+  }
+  item_off[n_images] = items;
+  meta->chunk_tiles = (int32_t)ch;
+  meta->items = items;
+  meta->overflow = items > item_cap ? 1 : 0;
+}
+
+// ---------------------------------------------------------------- reduce + exact map
+template <int B>
+__global__ void k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec,
+                               const int64_t* __restrict__ n_act,
+                               const int64_t* __restrict__ act_off,
+                               const int64_t* __restrict__ pool_off, int n_images, int L,
+                               const SelState* __restrict__ sel,
+                               const int64_t* __restrict__ item_off,
+                               const int32_t* __restrict__ chunks, const Cand* __restrict__ part,
+                               SSet S, int level, const PlanMeta* __restrict__ meta,
+                               uint32_t* __restrict__ status, fic_transform* __restrict__ res) {
+  constexpr int n = B * B;
+  const int64_t N = *n_act;
+  const bool overflow = meta->overflow != 0;
+  if (overflow && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusOverflow);
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const RangeRec r = rec[g];
+    const int im = r.img;
+    const int64_t l = g - act_off[im];
+    const int64_t m = l / kTileRanges;
+    const int rr = (int)(l % kTileRanges);
+    const int nc = overflow ? 0 : chunks[im];
+    Cand best{INT64_MAX, INT64_MAX};
+    for (int c = 0; c < nc; ++c) {
+      const Cand* p = part + (item_off[im] + m * nc + c) * kTileRows + rr * 8;
+      for (int k = 0; k < 8; ++k) {
+        const Cand x = p[k];
+        if (x.score < best.score || (x.score == best.score && x.key < best.key)) best = x;
+      }
+    }
+    fic_transform t{};
+    t.level = level;
+    t.x = r.x;
+    t.y = r.y;
+    t.size = B;
+    const ImgDev I = imgs[im];
+    const bool bad = best.key == INT64_MAX || best.key < 0 ||
+                     best.key / (8 * (int64_t)S.m) >= (int64_t)I.px * I.py;
+    if (bad) {  // no candidate (plan overflow): flagged, never read as a map
+      t.dom_index = -1;
+      t.e = INFINITY;
+      t.e_num = INT64_MAX;
+      res[g] = t;
+      continue;
+    }
+    const int s_idx = (int)(best.key % S.m);
+    const int iso = (int)((best.key / S.m) % 8);
+    const int pos = (int)(best.key / (8 * (int64_t)S.m));
+    const int dx = (pos % I.px) * L, dy = (pos / I.px) * L;
+    // Exact moments of the chosen pair: Eq. 1 with D = Ds / 4 and s = p / q.
+    int64_t sr = 0, sr2 = 0, sdd = 0, sdd2 = 0, cor = 0;
+    for (int i = 0; i < B; ++i)
+      for (int j = 0; j < B; ++j) {
+        int si, sj;
+        iso_src(B, iso, i, j, &si, &sj);
+        const uint8_t* pd = I.pix + (int64_t)(dy + 2 * si) * I.pitch + (dx + 2 * sj);
+        const int64_t ds = (int64_t)pd[0] + pd[1] + pd[I.pitch] + pd[I.pitch + 1];
+        const int64_t rv = I.pix[(int64_t)(r.y + i) * I.pitch + r.x + j];
+        sr += rv;
+        sr2 += rv * rv;
+        sdd += ds;
+        sdd2 += ds * ds;
+        cor += rv * ds;
+      }
+    const int64_t p = S.p[s_idx], q = S.q;
+    const int64_t A = n * sr2 - sr * sr;
+    const int64_t C = n * cor - sr * sdd;
+    const int64_t V = n * sdd2 - sdd * sdd;
+    // 16 q^2 n^2 E = n (16 q^2 A - 8 p q C + p^2 V)
+    const int64_t enum_ = (int64_t)n * (16 * q * q * A - 8 * p * q * C + p * p * V);
+    t.dom_index = pos;
+    t.dom_x = dx;
+    t.dom_y = dy;
+    t.iso = iso;
+    t.s_idx = s_idx;
+    t.p = (int32_t)p;
+    t.q = (int32_t)q;
+    t.e_num = enum_;
+    t.o_num = 4 * q * sr - p * sdd;  // Eq. 3 times 4 q n
+    t.e = (double)enum_ / (16.0 * (double)(q * q) * (double)n * (double)n);
+    t.s = (double)p / (double)q;
+    t.o = (double)t.o_num / (4.0 * (double)q * (double)n);
+    res[g] = t;
+  }
+}
+
+int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
+                        int64_t cap, const int64_t* act_off, const int64_t* pool_off,
+                        int n_images, int L, const SelState* sel, const int64_t* item_off,
+                        const int32_t* chunks, const Cand* part, const SSet& S, int level,
+                        const PlanMeta* meta, uint32_t* status, fic_transform* res,
+                        cudaStream_t st) {
+  const int threads = 128;
+  int grid = (int)ceil_div64(cap > 0 ? cap : 1, threads);
+  if (grid > 65535) grid = 65535;
+#define FIC_RF(BB)                                                                           \
+  k_reduce_final<BB><<<grid, threads, 0, st>>>(imgs, rec, n_act, act_off, pool_off, n_images, \
+                                               L, sel, item_off, chunks, part, S, level, meta, \
+                                               status, res)
+  switch (B) {
+    case 16: FIC_RF(16); break;
+    case 8: FIC_RF(8); break;
+    case 4: FIC_RF(4); break;
+    case 2: FIC_RF(2); break;
+    default: return FIC_EINVAL;
+  }
+#undef FIC_RF
+  return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
+}
+
+// ---------------------------------------------------------------- quadtree split
+// Accept when E <= n T^2, compared in double as (double) e_num / (16 q^2 n^2)
+// against n (T T); the last level accepts everything.
+__global__ void k_split_flags(const fic_transform* __restrict__ res,
+                              const RangeRec* __restrict__ rec, const int64_t* __restrict__ n_act,
+                              double e_thr, int last, uint8_t* __restrict__ acc,
+                              int32_t* __restrict__ acc_cnt, int32_t* __restrict__ rej_cnt) {
+  const int64_t N = *n_act;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const bool a = last || (res[g].e <= e_thr);
+    acc[g] = a ? 1 : 0;
+    atomicAdd(a ? &acc_cnt[rec[g].img] : &rej_cnt[rec[g].img], 1);
+  }
+}
+
+// Per-image offsets of the codes saved at this level and of the next level's
+// ranges (4 children per split range); images stay in order.
+__global__ void k_split_offsets(int n_images, const int32_t* __restrict__ acc_cnt,
+                                const int32_t* __restrict__ rej_cnt, int64_t* __restrict__ code_off,
+                                int64_t* __restrict__ next_off, int64_t* __restrict__ next_cnt,
+                                int64_t* __restrict__ next_n) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t a = 0, c = 0;
+  for (int i = 0; i < n_images; ++i) {
+    code_off[i] = a;
+    if (next_off) next_off[i] = c;
+    if (next_cnt) next_cnt[i] = 4 * (int64_t)rej_cnt[i];
+    a += acc_cnt[i];
+    c += 4 * (int64_t)rej_cnt[i];
+  }
+  code_off[n_images] = a;
+  if (next_off) next_off[n_images] = c;
+  if (next_n) *next_n = c;
+}
+
+struct SplitCompact {
+  const int64_t* n_act;
+  const uint8_t* acc;
+  const fic_transform* res;
+  const RangeRec* rec;
+  fic_transform* codes;
+  RangeRec* next;
+  int half;
+  __device__ int64_t size() const { return *n_act; }
+  __device__ bool flag(int64_t g) const { return acc[g] != 0; }
+  __device__ void emit(int64_t g, int64_t rank, bool f) const {
+    if (f) {
+      codes[rank] = res[g];
+    } else if (next) {
+      const RangeRec r = rec[g];
+      RangeRec* o = next + 4 * rank;
+      o[0] = RangeRec{r.img, r.x, r.y, (int32_t)g};
+      o[1] = RangeRec{r.img, r.x + half, r.y, (int32_t)g};
+      o[2] = RangeRec{r.img, r.x, r.y + half, (int32_t)g};
+      o[3] = RangeRec{r.img, r.x + half, r.y + half, (int32_t)g};
+    }
+  }
+};
+
+int launch_split(const fic_transform* res, const RangeRec* rec, const int64_t* n_act, int64_t cap,
+                 int B, double rms, int last, int n_images, uint8_t* acc, int32_t* acc_cnt,
+                 int32_t* rej_cnt, int64_t* code_off, fic_transform* codes, RangeRec* next,
+                 int64_t* next_off, int64_t* next_cnt, int64_t* next_n, int32_t* scan_scratch,
+                 int64_t* total, cudaStream_t st) {
+  const int n = B * B;
+  const double e_thr = (double)n * (rms * rms);
+  cudaMemsetAsync(acc_cnt, 0, sizeof(int32_t) * n_images, st);
+  cudaMemsetAsync(rej_cnt, 0, sizeof(int32_t) * n_images, st);
+  int grid = (int)ceil_div64(cap > 0 ? cap : 1, 256);
+  if (grid > 65535) grid = 65535;
+  k_split_flags<<<grid, 256, 0, st>>>(res, rec, n_act, e_thr, last, acc, acc_cnt, rej_cnt);
+  k_split_offsets<<<1, 32, 0, st>>>(n_images, acc_cnt, rej_cnt, code_off, next_off, next_cnt,
+                                     next_n);
+  SplitCompact sc{n_act, acc, res, rec, codes, next, B / 2};
+  FIC_CUDA_TRY(scan_compact(sc, cap, scan_scratch, total, st));
+  return FIC_OK;
+}
+
+}  // namespace fic

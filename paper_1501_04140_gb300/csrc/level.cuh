@@ -1,0 +1,66 @@
+// level.cuh -- launchers of the per-level steps and the matcher interface.
+#pragma once
+
+#include "fic_internal.h"
+
+namespace fic {
+
+struct PlanMeta {
+  int64_t items;        // work items of the level
+  int32_t chunk_tiles;  // 128-domain tiles per item (the last chunk may be shorter)
+  int32_t overflow;     // 1 if items exceeded the capacity (nothing matched)
+};
+
+// Everything a matcher launch needs (device pointers).
+struct MatchArgs {
+  int B, n, Kp, n_images;
+  SSet S;
+  float delta;                      // screening margin in score units (tensor path)
+  const RangeMom* mom;              // per range
+  const uint16_t* apack;            // f16 rows, core-matrix layout
+  const float* a32;                 // fp32 rows
+  const uint16_t* bpack;            // f16 domains, core-matrix layout
+  const float* b32;                 // fp32 domains
+  const DomRec* dom;                // per domain slot
+  const float4* domf;               // per domain slot: {SD', u0, u1 | g, 0}
+  const int64_t* act_off;           // n_images + 1 (ranges)
+  const int64_t* act_cnt;           // n_images
+  const int64_t* pool_off;          // n_images + 1 (domain slots)
+  const SelState* sel;              // n_kept per image
+  const int64_t* item_off;          // n_images + 1
+  const int32_t* chunks;            // per image
+  const PlanMeta* meta;
+  Cand* part;                       // items x 128
+  uint32_t* status;                 // device status word
+};
+
+int launch_range_pack(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
+                      int64_t cap, int Kp, RangeMom* mom, uint16_t* apack, float* a32,
+                      cudaStream_t st);
+
+__global__ void k_plan(int n_images, const int64_t* act_off, const int64_t* act_cnt,
+                       const SelState* sel, int target_items, int64_t item_cap, int64_t mt_cap,
+                       PlanMeta* meta, int64_t* item_off, int32_t* chunks);
+
+int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
+                        int64_t cap, const int64_t* act_off, const int64_t* pool_off,
+                        int n_images, int L, const SelState* sel, const int64_t* item_off,
+                        const int32_t* chunks, const Cand* part, const SSet& S, int level,
+                        const PlanMeta* meta, uint32_t* status, fic_transform* res,
+                        cudaStream_t st);
+
+int launch_split(const fic_transform* res, const RangeRec* rec, const int64_t* n_act, int64_t cap,
+                 int B, double rms, int last, int n_images, uint8_t* acc, int32_t* acc_cnt,
+                 int32_t* rej_cnt, int64_t* code_off, fic_transform* codes, RangeRec* next,
+                 int64_t* next_off, int64_t* next_cnt, int64_t* next_n, int32_t* scan_scratch,
+                 int64_t* total, cudaStream_t st);
+
+// Matchers: fill args.part for every planned item.  `grid` persistent CTAs.
+int launch_match_f32(const MatchArgs& a, int grid, cudaStream_t st);
+int launch_match_tc(const MatchArgs& a, int grid, cudaStream_t st);
+int match_tc_prepare();  // per device, before the first launch
+
+// Screening margin of the tensor path's float scores (score units, E'/(8qn)).
+float screening_delta(int B, const SSet& S);
+
+}  // namespace fic

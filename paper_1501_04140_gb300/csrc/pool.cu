@@ -1,0 +1,397 @@
+// pool.cu -- the entropy-filtered domain pool of one quadtree level (Sec. 2
+// domain pool, Sec. 3 entropy filter) for a batch of images.
+//
+//   k_pool_stats    every 2B x 2B square at step L: its entropy key (Eq. 4-5,
+//                   fixed point), the sum of its 2x2 sums Ds and of Ds^2.
+//   k_sel_*         exact percentile threshold of the keys (radix select,
+//                   5 passes of 9 bits), per image.
+//   compaction      kept = entropy greater than the threshold (key below it),
+//                   ascending raster order; "greater or equal" when that keeps
+//                   nothing.
+//   k_pack_domains  the kept domains as matcher operands: f16 (Ds - 512) in
+//                   the tensor cores' K-major core-matrix layout and/or fp32,
+//                   plus the per-domain moments the scoring needs.
+#include <math.h>
+
+#include "fic_internal.h"
+#include "scan.cuh"
+
+namespace fic {
+
+// ---------------------------------------------------------------- S sets
+void make_sset(int s_mode, int grid_samples, int B, SSet* o) {
+  *o = SSet{};
+  if (s_mode == FIC_S_GRID) {
+    o->grid = 1;
+    o->m = grid_samples;
+    o->q = grid_samples - 1;
+    for (int k = 0; k < grid_samples && k < kMaxS; ++k) o->p[k] = k;
+    return;
+  }
+  // Sec. 3.1: step 1 (B = 16) {0.1}; step 2 (B = 8) {0.2, 0.4};
+  // step 3 (B = 4) {0.3, 0.8}; step 4 (B = 2) {0.5, 0.9}.
+  o->grid = 0;
+  o->q = 10;
+  switch (B) {
+    case 16: o->m = 1; o->p[0] = 1; break;
+    case 8: o->m = 2; o->p[0] = 2; o->p[1] = 4; break;
+    case 4: o->m = 2; o->p[0] = 3; o->p[1] = 8; break;
+    default: o->m = 2; o->p[0] = 5; o->p[1] = 9; break;
+  }
+}
+
+// ---------------------------------------------------------------- entropy key table
+// Key of a histogram: sum over grey levels of round(c ln c 2^32), c the
+// level's count (Eq. 4-5 with the constant ln(#pixels) and the 1/#pixels
+// factor dropped: H = ln N - key / (N 2^32), so a larger key is a lower
+// entropy).  The device accumulates it per pixel as the increments
+// dT[c] = T[c] - T[c - 1] of the running count, so no bin scan is needed.
+int host_key_table(int64_t* dT, int nmax) {
+  int64_t prev = 0;
+  dT[0] = 0;
+  for (int c = 1; c <= nmax; ++c) {
+    long double v = (long double)c * logl((long double)c) * 4294967296.0L;
+    int64_t t = (int64_t)llroundl(v);
+    dT[c] = t - prev;
+    prev = t;
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------- pool statistics
+// G lanes per domain (G = min(32, B^2)); each lane takes whole 2x2 cells.
+template <int B>
+struct PoolGeom {
+  static constexpr int n = B * B;
+  static constexpr int G = n < 32 ? n : 32;
+  static constexpr int GPB = 16;             // groups (domains) per block
+  static constexpr int threads = G * GPB;
+};
+
+template <int B>
+__global__ void __launch_bounds__(PoolGeom<B>::threads)
+k_pool_stats(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off, int n_images,
+             int L, const int64_t* __restrict__ dT_g, int64_t* __restrict__ keys,
+             int32_t* __restrict__ sd, int32_t* __restrict__ sq) {
+  using Gm = PoolGeom<B>;
+  constexpr int G = Gm::G;
+  constexpr int N4 = 4 * B * B;
+  __shared__ uint32_t hist[Gm::GPB][256];
+  __shared__ int64_t dT[N4 + 1];
+  for (int i = threadIdx.x; i <= N4; i += blockDim.x) dT[i] = dT_g[i];
+  for (int i = threadIdx.x; i < Gm::GPB * 256; i += blockDim.x) (&hist[0][0])[i] = 0;
+  __syncthreads();
+
+  const int grp = threadIdx.x / G, gl = threadIdx.x % G;
+  uint32_t* h = hist[grp];
+  const int64_t P_tot = off[n_images];
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+  for (int64_t g = (int64_t)blockIdx.x * Gm::GPB + grp; g < P_tot; g += (int64_t)gridDim.x * Gm::GPB) {
+    const int im = find_segment(off, n_images, g);
+    const ImgDev I = imgs[im];
+    const int64_t pos = g - off[im];
+    const int x0 = (int)(pos % I.px) * L, y0 = (int)(pos / I.px) * L;
+    int64_t key = 0;
+    int s = 0, s2 = 0;
+    for (int c = gl; c < B * B; c += G) {
+      const int ci = c / B, cj = c % B;
+      const uint8_t* p = I.pix + (int64_t)(y0 + 2 * ci) * I.pitch + (x0 + 2 * cj);
+      const int v0 = p[0], v1 = p[1], v2 = p[I.pitch], v3 = p[I.pitch + 1];
+      key += dT[atomicAdd(&h[v0], 1u) + 1];
+      key += dT[atomicAdd(&h[v1], 1u) + 1];
+      key += dT[atomicAdd(&h[v2], 1u) + 1];
+      key += dT[atomicAdd(&h[v3], 1u) + 1];
+      const int ds = v0 + v1 + v2 + v3;
+      s += ds;
+      s2 += ds * ds;
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      key += __shfl_xor_sync(gmask, key, o, G);
+      s += __shfl_xor_sync(gmask, s, o, G);
+      s2 += __shfl_xor_sync(gmask, s2, o, G);
+    }
+    __syncwarp(gmask);
+    for (int c = gl; c < B * B; c += G) {  // clear the bins this lane touched
+      const int ci = c / B, cj = c % B;
+      const uint8_t* p = I.pix + (int64_t)(y0 + 2 * ci) * I.pitch + (x0 + 2 * cj);
+      h[p[0]] = 0; h[p[1]] = 0; h[p[I.pitch]] = 0; h[p[I.pitch + 1]] = 0;
+    }
+    __syncwarp(gmask);
+    if (gl == 0) {
+      keys[g] = key;
+      sd[g] = s;
+      sq[g] = s2;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- exact percentile
+// Sec. 3 keeps domains whose entropy is greater than a threshold; the
+// threshold is the pool's entropy at percentile p: sorted ascending by
+// entropy, index floor(p (P - 1)).  Entropy ascending is key descending, so
+// the threshold is the key of ascending rank P - 1 - floor(p (P - 1)).
+__global__ void k_sel_init(const int64_t* __restrict__ off, int n_images, double pct,
+                           SelState* __restrict__ st, uint32_t* __restrict__ hist) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_images * kSelBins;
+       i += gridDim.x * blockDim.x)
+    hist[i] = 0;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_images) {
+    int64_t P = off[i + 1] - off[i];
+    int64_t ih = (int64_t)floor(pct * (double)(P - 1));
+    if (ih < 0) ih = 0;
+    if (ih > P - 1) ih = P - 1;
+    SelState s{};
+    s.prefix = 0;
+    s.rank = (P > 0) ? (P - 1 - ih) : 0;
+    s.nlt = 0;
+    st[i] = s;
+  }
+}
+
+constexpr int kSelThreads = 256;
+constexpr int kSelPerThread = 16;
+
+__global__ void __launch_bounds__(kSelThreads)
+k_sel_hist(const int64_t* __restrict__ keys, const int64_t* __restrict__ off, int n_images,
+           int shift, const SelState* __restrict__ st, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[kSelBins];
+  for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const int64_t P_tot = off[n_images];
+  const int64_t b0 = (int64_t)blockIdx.x * kSelThreads * kSelPerThread;
+  const int im0 = b0 < P_tot ? find_segment(off, n_images, b0) : 0;
+  const int64_t pre0 = st[im0].prefix;
+  for (int t = 0; t < kSelPerThread; ++t) {
+    int64_t g = b0 + (int64_t)t * kSelThreads + threadIdx.x;
+    if (g >= P_tot) break;
+    const int64_t k = keys[g];
+    if (g >= off[im0 + 1] || g < off[im0]) {  // block straddles images
+      int im = find_segment(off, n_images, g);
+      if ((k >> (shift + kSelBits)) == st[im].prefix)
+        atomicAdd(&hist[im * kSelBins + ((k >> shift) & (kSelBins - 1))], 1u);
+    } else if ((k >> (shift + kSelBits)) == pre0) {
+      atomicAdd(&sh[(k >> shift) & (kSelBins - 1)], 1u);
+    }
+  }
+  __syncthreads();
+  if (b0 < P_tot)
+    for (int i = threadIdx.x; i < kSelBins; i += blockDim.x)
+      if (sh[i]) atomicAdd(&hist[im0 * kSelBins + i], sh[i]);
+}
+
+// One block of kSelBins threads per image: pick the digit holding the rank.
+__global__ void __launch_bounds__(kSelBins)
+k_sel_find(SelState* __restrict__ st, uint32_t* __restrict__ hist, int last) {
+  __shared__ int sw[32];
+  __shared__ int tot;
+  const int im = blockIdx.x;
+  uint32_t* h = hist + (int64_t)im * kSelBins;
+  const int c = (int)h[threadIdx.x];
+  const int before = block_excl_scan(c, sw, &tot);
+  SelState s = st[im];
+  __syncthreads();
+  if (tot > 0 && before <= s.rank && s.rank < before + c) {
+    s.prefix = (s.prefix << kSelBits) | threadIdx.x;
+    s.rank -= before;
+    s.nlt += before;
+    if (last) {
+      s.thr = s.prefix;
+      s.nle = s.nlt + c;
+      s.fallback = (s.nlt == 0) ? 1 : 0;
+      s.nkept = (int32_t)(s.fallback ? s.nle : s.nlt);
+    }
+    st[im] = s;
+  }
+  h[threadIdx.x] = 0;
+}
+
+__global__ void k_sel_bases(SelState* st, int n_images) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int64_t b = 0;
+    for (int i = 0; i < n_images; ++i) {
+      st[i].base = b;
+      b += st[i].nkept;
+    }
+  }
+}
+
+struct KeptCompact {
+  const int64_t* keys;
+  const int64_t* off;
+  const int64_t* slot_off;
+  const SelState* st;
+  int32_t* kept;
+  int n_images;
+  __device__ int64_t size() const { return off[n_images]; }
+  __device__ bool flag(int64_t g) const {
+    const int im = find_segment(off, n_images, g);
+    const SelState& s = st[im];
+    return s.fallback ? keys[g] <= s.thr : keys[g] < s.thr;
+  }
+  __device__ void emit(int64_t g, int64_t rank, bool f) const {
+    if (!f) return;
+    const int im = find_segment(off, n_images, g);
+    kept[slot_off[im] + (rank - st[im].base)] = (int32_t)(g - off[im]);
+  }
+};
+
+// ---------------------------------------------------------------- operand packing
+// f16 bits of a small integer (|v| <= 2048, exact in binary16).
+__device__ inline uint16_t f16_bits(int v) {
+  return __half_as_ushort(__int2half_rn(v));
+}
+
+// Tensor operand layout of the kept domains: for each 128-slot tile T and
+// K slice kc (one slice of 128 at B = 16, the whole padded K otherwise), the
+// tile's 16 groups of 8 domains, each as K/8 core matrices of 8 domains x 8
+// f16 (16-byte rows): [T][kc][group][k / 8][slot % 8][k % 8].  A (T, kc)
+// slice is contiguous and is copied to shared memory as it is.
+template <int B>
+struct PackGeom {
+  static constexpr int n = B * B;
+  static constexpr int Kp = n < 16 ? 16 : n;
+  static constexpr int NKC = n > 128 ? n / 128 : 1;
+  static constexpr int KS = Kp / NKC;
+};
+
+template <int B>
+__device__ inline int64_t bpack_index(int64_t slot, int e) {
+  using P = PackGeom<B>;
+  const int64_t T = slot >> 7;
+  const int r = (int)(slot & 127);
+  const int kc = e / P::KS, ek = e % P::KS;
+  return ((((T * P::NKC + kc) * 16 + (r >> 3)) * (P::KS / 8) + (ek >> 3)) * 8 + (r & 7)) * 8 +
+         (ek & 7);
+}
+
+template <int B>
+__global__ void __launch_bounds__(PoolGeom<B>::threads)
+k_pack_domains(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
+               const int64_t* __restrict__ slot_off, int n_images, int L,
+               const SelState* __restrict__ st, const int32_t* __restrict__ kept,
+               const int32_t* __restrict__ sd, const int32_t* __restrict__ sq, SSet S,
+               uint16_t* __restrict__ bpack, float* __restrict__ b32, DomRec* __restrict__ dom,
+               float4* __restrict__ domf) {
+  using Gm = PoolGeom<B>;
+  constexpr int G = Gm::G;
+  constexpr int n = B * B;
+  constexpr int Kp = PackGeom<B>::Kp;
+  const int grp = threadIdx.x / G, gl = threadIdx.x % G;
+  const int64_t S_tot = slot_off[n_images];
+  for (int64_t slot = (int64_t)blockIdx.x * Gm::GPB + grp; slot < S_tot;
+       slot += (int64_t)gridDim.x * Gm::GPB) {
+    const int im = find_segment(slot_off, n_images, slot);
+    const int64_t j = slot - slot_off[im];
+    if (j >= st[im].nkept) continue;
+    const ImgDev I = imgs[im];
+    const int32_t pos = kept[slot];
+    const int64_t gpos = off[im] + pos;
+    const int x0 = (pos % I.px) * L, y0 = (pos / I.px) * L;
+    for (int c = gl; c < n; c += G) {
+      const int ci = c / B, cj = c % B;
+      const uint8_t* p = I.pix + (int64_t)(y0 + 2 * ci) * I.pitch + (x0 + 2 * cj);
+      const int ds = p[0] + p[1] + p[I.pitch] + p[I.pitch + 1];
+      if (bpack) bpack[bpack_index<B>(slot, c)] = f16_bits(ds - 512);
+      if (b32) b32[slot * n + c] = (float)(ds - 512);
+    }
+    if (bpack && n < Kp)  // zero the K padding (B = 2: K = 4 of 16)
+      for (int c = n + gl; c < Kp; c += G) bpack[bpack_index<B>(slot, c)] = 0;
+    if (gl == 0) {
+      const int64_t s = sd[gpos], s2 = sq[gpos];
+      DomRec r;
+      r.v = (int64_t)n * s2 - s * s;
+      r.sdp = (int32_t)(s - 512 * n);
+      r.pos = pos;
+      dom[slot] = r;
+      // Scores are E' / (8 q n) with E' = p^2 V - 8 p q C (see the match
+      // kernels): explicit sets store p_t^2 V / (8 q n); the grid stores
+      // V / (8 q n) and 4 q n / V, the scale of the real minimiser
+      // p* = 4 q C / V.
+      const double u = (double)r.v / (8.0 * S.q * n);
+      float4 f;
+      f.x = (float)r.sdp;
+      if (S.grid) {
+        f.y = (float)u;
+        f.z = r.v > 0 ? (float)(4.0 * S.q * n / (double)r.v) : 0.0f;
+        f.w = 0.0f;
+      } else {
+        f.y = (float)(u * S.p[0] * S.p[0]);
+        f.z = S.m > 1 ? (float)(u * S.p[1] * S.p[1]) : 0.0f;
+        f.w = 0.0f;
+      }
+      domf[slot] = f;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- driver
+template <int B>
+static int pool_build_B(PoolLevel& pl, const int64_t* d_dT, cudaStream_t st) {
+  using Gm = PoolGeom<B>;
+  const int ni = pl.n_images;
+  const int64_t P = pl.P_tot;
+  const int nsm = pl.nsm > 0 ? pl.nsm : 148;
+  const int64_t groups = ceil_div64(P > 0 ? P : 1, Gm::GPB);
+  const int grid = (int)(groups < (int64_t)nsm * 16 ? groups : (int64_t)nsm * 16);
+  k_pool_stats<B><<<grid, Gm::threads, 0, st>>>(pl.img.as<ImgDev>(), pl.off.as<int64_t>(), ni,
+                                                pl.L, d_dT, pl.keys.as<int64_t>(),
+                                                pl.sd.as<int32_t>(), pl.sq.as<int32_t>());
+  return FIC_OK;
+}
+
+int pool_build(PoolLevel& pl, const int64_t* d_dT, cudaStream_t st) {
+  const double pct = pl.pct;
+  const int ni = pl.n_images;
+  const int64_t P = pl.P_tot;
+  int rc = FIC_OK;
+  switch (pl.B) {
+    case 16: rc = pool_build_B<16>(pl, d_dT, st); break;
+    case 8: rc = pool_build_B<8>(pl, d_dT, st); break;
+    case 4: rc = pool_build_B<4>(pl, d_dT, st); break;
+    case 2: rc = pool_build_B<2>(pl, d_dT, st); break;
+    default: return FIC_EINVAL;
+  }
+  if (rc) return rc;
+  SelState* sel = pl.sel.as<SelState>();
+  uint32_t* hist = pl.hist.as<uint32_t>();
+  const int64_t* off = pl.off.as<int64_t>();
+  k_sel_init<<<ceil_div(ni * kSelBins, 256), 256, 0, st>>>(off, ni, pct, sel, hist);
+  const int nb = (int)ceil_div64(P > 0 ? P : 1, (int64_t)kSelThreads * kSelPerThread);
+  for (int pass = 0; pass < kSelPasses; ++pass) {
+    const int shift = (kSelPasses - 1 - pass) * kSelBits;
+    k_sel_hist<<<nb, kSelThreads, 0, st>>>(pl.keys.as<int64_t>(), off, ni, shift, sel, hist);
+    k_sel_find<<<ni, kSelBins, 0, st>>>(sel, hist, pass == kSelPasses - 1);
+  }
+  k_sel_bases<<<1, 32, 0, st>>>(sel, ni);
+  KeptCompact kc{pl.keys.as<int64_t>(), off, pl.slot_off.as<int64_t>(), sel,
+                 pl.kept.as<int32_t>(), ni};
+  FIC_CUDA_TRY(scan_compact(kc, P, pl.scan_scratch.as<int32_t>(), pl.total.as<int64_t>(), st));
+
+  const int nsm = pl.nsm > 0 ? pl.nsm : 148;
+  uint16_t* bp = pl.want_tc ? pl.bpack.as<uint16_t>() : nullptr;
+  float* b32 = pl.want_f32 ? pl.b32.as<float>() : nullptr;
+#define FIC_PACK(BB)                                                                           \
+  {                                                                                            \
+    using Gm = PoolGeom<BB>;                                                                   \
+    const int64_t groups = ceil_div64(pl.S_tot > 0 ? pl.S_tot : 1, Gm::GPB);                  \
+    const int grid = (int)(groups < (int64_t)nsm * 16 ? groups : (int64_t)nsm * 16);          \
+    k_pack_domains<BB><<<grid, Gm::threads, 0, st>>>(                                          \
+        pl.img.as<ImgDev>(), off, pl.slot_off.as<int64_t>(), ni, pl.L, sel,                    \
+        pl.kept.as<int32_t>(),                                                                 \
+        pl.sd.as<int32_t>(), pl.sq.as<int32_t>(), pl.sset, bp, b32, pl.dom.as<DomRec>(),       \
+        pl.domf.as<float4>());                                                                 \
+  }
+  switch (pl.B) {
+    case 16: FIC_PACK(16) break;
+    case 8: FIC_PACK(8) break;
+    case 4: FIC_PACK(4) break;
+    default: FIC_PACK(2) break;
+  }
+#undef FIC_PACK
+  FIC_CUDA_TRY(cudaGetLastError());
+  return FIC_OK;
+}
+
+}  // namespace fic

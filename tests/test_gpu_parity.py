@@ -1,0 +1,322 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bars (from the method's arithmetic): integer work (entropy keys, kept lists,
+moments, the exact tensor path's chosen error numerators and tie-break keys)
+bit-exact; the FP32 path's choice within its derived rounding bound; decoded
+images identical (same FP64 operation order) or PSNR within 0.01 dB.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1501_04140_gb300.synth import synth_image
+from tests import gpu_util as G
+
+pytestmark = pytest.mark.gpu
+
+PREC = {"tensor": 0, "fp32": 1}
+
+
+def _fic():
+    G.ctx()
+    from paper_1501_04140_gb300 import fic
+    return fic
+
+
+def _ramp(W, H):
+    x = np.arange(W)[None, :].repeat(H, 0)
+    return (x % 256).astype(np.uint8)
+
+
+def _flat(W, H, v=77):
+    return np.full((H, W), v, np.uint8)
+
+
+POOL_CASES = [
+    # (image, B, L, percentile)
+    (lambda: synth_image(64, 64, 3), 8, 2, 0.5),
+    (lambda: synth_image(96, 64, 4, n_textured=1), 16, 1, 0.75),
+    (lambda: synth_image(128, 128, 1), 8, 4, 0.5),
+    (lambda: synth_image(40, 32, 6), 2, 2, 0.5),
+    (lambda: synth_image(48, 32, 7), 4, 3, 0.25),
+    (lambda: _flat(32, 32), 8, 2, 0.5),
+    (lambda: synth_image(64, 64, 8), 16, 2, 1.0),
+    (lambda: synth_image(64, 64, 8), 16, 2, 0.0),
+]
+
+
+@pytest.mark.parametrize("case", range(len(POOL_CASES)))
+@pytest.mark.parametrize("prec", ["tensor", "fp32"])
+def test_pool_parity(case, prec):
+    fic = _fic()
+    mk, B, L, pct = POOL_CASES[case]
+    img = mk()
+    ctx = G.ctx()
+    p = fic.default_params(domain_step=L, entropy_percentile=pct, precision=PREC[prec])
+    pool = ctx.build_domain_pool(G.dev(img), B, p)
+    info = pool.info()
+    keys_o, kept_o, thr_o, fb_o = oracle.pool_filter(img, B, L, pct)
+    P, px, py = oracle.pool_size(img.shape[1], img.shape[0], B, L)
+    assert info["pool_size"] == P and info["px"] == px and info["py"] == py
+    np.testing.assert_array_equal(pool.copy(fic.FIC_POOL_KEYS), keys_o)
+    assert info["thr_key"] == thr_o
+    assert info["fallback"] == fb_o
+    kept = pool.copy(fic.FIC_POOL_KEPT)
+    np.testing.assert_array_equal(kept, kept_o)
+    sums = pool.copy(fic.FIC_POOL_SUMS)
+    sq = pool.copy(fic.FIC_POOL_SQSUMS)
+    for j in range(0, len(kept_o), max(1, len(kept_o) // 50)):
+        d = int(kept_o[j])
+        Ds = oracle.decimate(img, (d % px) * L, (d // px) * L, B)
+        assert sums[j] == Ds.sum()
+        assert sq[j] == (Ds * Ds).sum()
+    pool.free()
+
+
+MATCH_CASES = [
+    # (W, H, seed, B, L, s_mode, grid, n_ranges or None (all))
+    (64, 64, 5, 8, 2, 0, 16, None),
+    (64, 64, 5, 8, 1, 0, 16, 37),
+    (96, 96, 9, 16, 2, 0, 16, None),
+    (64, 48, 10, 4, 2, 0, 16, 150),
+    (32, 32, 11, 2, 1, 0, 16, 200),
+    (64, 64, 12, 8, 2, 1, 16, None),
+    (64, 64, 13, 8, 3, 1, 32, 50),
+    (96, 64, 14, 16, 1, 1, 16, 20),
+    (48, 48, 15, 2, 2, 1, 10, 120),
+    (64, 64, 16, 4, 1, 1, 16, 90),
+]
+
+
+def _ranges(W, H, B, n, seed):
+    xy = np.array([(x, y) for y in range(0, H - B + 1, B) for x in range(0, W - B + 1, B)],
+                  np.int32)
+    if n is None or n >= len(xy):
+        return xy
+    rng = np.random.default_rng(seed)
+    # arbitrary positions too (not only the range grid)
+    out = []
+    for i in range(n):
+        if i % 3 == 0:
+            out.append((rng.integers(0, W - B + 1), rng.integers(0, H - B + 1)))
+        else:
+            out.append(tuple(xy[rng.integers(0, len(xy))]))
+    return np.array(out, np.int32)
+
+
+@pytest.mark.parametrize("case", range(len(MATCH_CASES)))
+@pytest.mark.parametrize("prec", ["tensor", "fp32"])
+def test_match_level_parity(case, prec):
+    fic = _fic()
+    W, H, seed, B, L, smode, M, nr = MATCH_CASES[case]
+    img = synth_image(W, H, seed, n_textured=1)
+    ctx = G.ctx()
+    p = fic.default_params(domain_step=L, s_mode=smode, grid_samples=M, precision=PREC[prec])
+    d = G.dev(img)
+    pool = ctx.build_domain_pool(d, B, p)
+    rxy = _ranges(W, H, B, nr, seed)
+    got = ctx.match_level(d, pool, rxy, p)
+    pool.free()
+    _, kept, _, _ = oracle.pool_filter(img, B, L, 0.5)
+    sp, q = oracle.s_set(smode, M, B)
+    ref = oracle.match(img, B, L, kept, rxy, sp, q, n_threads=8)
+    assert len(got) == len(ref)
+    n_s = len(sp)
+    if prec == "tensor":
+        np.testing.assert_array_equal(got["e_num"], ref["e_num"])
+        np.testing.assert_array_equal(G.keys_of(got, n_s), ref["key"])
+    else:
+        tol = G.fp32_enum_tol(B, sp, q)
+        assert np.all(got["e_num"] >= ref["e_num"])
+        assert np.all(got["e_num"] - ref["e_num"] <= tol), (got["e_num"] - ref["e_num"]).max()
+    # the exact map of the chosen candidate (Eq. 1, Eq. 3) for every range
+    n = B * B
+    for i in range(0, len(got), max(1, len(got) // 20)):
+        g = got[i]
+        R = img[g["y"]:g["y"] + B, g["x"]:g["x"] + B].astype(np.int64)
+        Ds = oracle.isometry(oracle.decimate(img, g["dom_x"], g["dom_y"], B), g["iso"])
+        assert g["e_num"] == oracle.error_num(R, Ds, int(g["p"]), int(g["q"]))
+        assert g["o_num"] == 4 * g["q"] * R.sum() - g["p"] * Ds.sum()
+        assert g["e"] == g["e_num"] / (16.0 * g["q"] * g["q"] * n * n)
+
+
+ENC_CASES = [
+    # (W, H, seed, textured, params)
+    (96, 96, 21, 1, dict()),
+    (64, 96, 22, 1, dict(s_mode=1, grid_samples=16)),
+    (64, 64, 23, 0, dict(range_size0=8, n_levels=3, domain_step=1)),
+    (128, 128, 1, 0, dict(range_size0=8, single_level=1, domain_step=4, s_mode=1,
+                          grid_samples=16)),
+    (48, 80, 24, 1, dict(entropy_percentile=0.75, rms_threshold=5.0)),
+    (64, 64, 25, 1, dict(range_size0=4, n_levels=2, domain_step=2, rms_threshold=3.0)),
+]
+
+
+def _enc_params(fic, prec, kw):
+    p = fic.default_params(precision=PREC[prec])
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("case", range(len(ENC_CASES)))
+def test_encode_parity_tensor(case):
+    fic = _fic()
+    W, H, seed, tex, kw = ENC_CASES[case]
+    img = synth_image(W, H, seed, n_textured=tex)
+    ctx = G.ctx()
+    p = _enc_params(fic, "tensor", kw)
+    code = ctx.encode(G.dev(img), p)
+    got = code.transforms(0)
+    ref, rstats = oracle.encode(img, G.oracle_params(p))
+    assert len(got) == len(ref)
+    for f in ("level", "x", "y", "size", "dom_index", "dom_x", "dom_y", "iso", "s_idx", "p", "q",
+              "e_num", "o_num", "e", "s", "o"):
+        np.testing.assert_array_equal(got[f], ref[f], err_msg=f)
+    st = code.stats(0)
+    for a, b in zip(st, rstats):
+        for f in ("size", "pool_size", "n_kept", "fallback", "thr_key", "n_active", "n_accepted"):
+            assert a[f] == b[f], (f, a, b)
+    # decoder: identical iterate to the oracle's on the same codes
+    dec = code.decode(0)
+    ref_f, it = oracle.decode(ref, W, H)
+    np.testing.assert_array_equal(dec, oracle.to_u8(ref_f))
+    assert code.iters == it
+    code.free()
+
+
+@pytest.mark.parametrize("case", [0, 1, 4])
+def test_encode_fp32_psnr(case):
+    fic = _fic()
+    W, H, seed, tex, kw = ENC_CASES[case]
+    img = synth_image(W, H, seed, n_textured=tex)
+    ctx = G.ctx()
+    p = _enc_params(fic, "fp32", kw)
+    code = ctx.encode(G.dev(img), p)
+    dec = code.decode(0)
+    ref, _ = oracle.encode(img, G.oracle_params(p))
+    ref_f, _ = oracle.decode(ref, W, H)
+    a = oracle.psnr(img, dec)
+    b = oracle.psnr(img, oracle.to_u8(ref_f))
+    assert abs(a - b) <= 0.01, (a, b)
+    code.free()
+
+
+def test_encode_batch_uneven_sizes():
+    fic = _fic()
+    ctx = G.ctx()
+    sizes = [(64, 64), (96, 48), (32, 32), (128, 64)]
+    imgs = [synth_image(W, H, 40 + i, n_textured=1) for i, (W, H) in enumerate(sizes)]
+    p = fic.default_params()
+    code = ctx.encode([G.dev(im) for im in imgs], p)
+    for i, im in enumerate(imgs):
+        got = code.transforms(i)
+        ref, rstats = oracle.encode(im, G.oracle_params(p))
+        np.testing.assert_array_equal(got["e_num"], ref["e_num"])
+        np.testing.assert_array_equal(got["dom_index"], ref["dom_index"])
+        np.testing.assert_array_equal(got["x"], ref["x"])
+        np.testing.assert_array_equal(got["level"], ref["level"])
+        st = code.stats(i)
+        assert [s["n_active"] for s in st] == [s["n_active"] for s in rstats]
+    code.free()
+
+
+def test_encode_host_image_and_again():
+    fic = _fic()
+    ctx = G.ctx()
+    img = synth_image(64, 64, 50, n_textured=1)
+    p = fic.default_params()
+    code = ctx.encode(img, p)  # host numpy array: the library copies it
+    ref, _ = oracle.encode(img, G.oracle_params(p))
+    np.testing.assert_array_equal(code.transforms(0)["e_num"], ref["e_num"])
+    img2 = synth_image(64, 64, 51, n_textured=1)
+    ctx.encode_again(code, img2, p)
+    ref2, _ = oracle.encode(img2, G.oracle_params(p))
+    got2 = code.transforms(0)
+    np.testing.assert_array_equal(got2["e_num"], ref2["e_num"])
+    np.testing.assert_array_equal(got2["dom_index"], ref2["dom_index"])
+    code.free()
+
+
+def test_flat_image_exact():
+    fic = _fic()
+    ctx = G.ctx()
+    img = _flat(64, 64, 90)
+    p = fic.default_params(rms_threshold=0.0)
+    code = ctx.encode(G.dev(img), p)
+    t = code.transforms(0)
+    st = code.stats(0)
+    assert st[0]["fallback"] == 1
+    assert np.all(t["e_num"] == 0)
+    assert len(t) == 16  # every 16x16 range accepted at level 0 with E = 0
+    dec = code.decode(0)
+    np.testing.assert_array_equal(dec, img)
+    code.free()
+
+
+def test_ramp_reconstructs_exactly():
+    """An integer ramp f = x: the decimated domain has twice the slope, so
+    s = 0.5 (Sec. 3.1's step-4 set) with the identity reproduces it with
+    E = 0 at the 2x2 level (threshold 0 forces the descent)."""
+    fic = _fic()
+    ctx = G.ctx()
+    img = _ramp(128, 64)
+    p = fic.default_params(rms_threshold=0.0)
+    code = ctx.encode(G.dev(img), p)
+    t = code.transforms(0)
+    ref, _ = oracle.encode(img, G.oracle_params(p))
+    np.testing.assert_array_equal(t["e_num"], ref["e_num"])
+    assert np.all(t["e_num"][t["level"] == 3] == 0)
+    code.free()
+
+
+def test_invalid_arguments():
+    fic = _fic()
+    ctx = G.ctx()
+    img = synth_image(64, 64, 1)
+    p = fic.default_params()
+    with pytest.raises(fic.FicError) as e:
+        ctx.encode(G.dev(img[:, :40]), p)  # width not a multiple of 16
+    assert e.value.status == fic.FIC_EINVAL
+    bad = fic.default_params(range_size0=3)
+    with pytest.raises(fic.FicError):
+        ctx.encode(G.dev(img), bad)
+    pool = ctx.build_domain_pool(G.dev(img), 8, p)
+    with pytest.raises(fic.FicError):
+        ctx.match_level(G.dev(img), pool, np.array([[60, 60]], np.int32), p)  # outside
+    pool.free()
+
+
+# ------------------------------------------------------------- full size
+def test_paper_scale_sampled_parity():
+    """512 x 512, full quadtree, L = 2, predefined S (the headline workload):
+    every level's pool keys and kept list in full, and a sample of each
+    level's saved maps re-derived by the oracle's exhaustive search."""
+    fic = _fic()
+    ctx = G.ctx()
+    img = synth_image(512, 512, 1, n_textured=1)
+    p = fic.default_params()
+    code = ctx.encode(G.dev(img), p)
+    t = code.transforms(0)
+    st = code.stats(0)
+    rng = np.random.default_rng(0)
+    for lv in range(4):
+        B = 16 >> lv
+        keys_o, kept_o, thr_o, fb_o = oracle.pool_filter(img, B, 2, 0.5)
+        assert st[lv]["thr_key"] == thr_o and st[lv]["n_kept"] == len(kept_o)
+        rows = t[t["level"] == lv]
+        if len(rows) == 0:
+            continue
+        pick = rows[rng.choice(len(rows), size=min(6, len(rows)), replace=False)]
+        sp, q = oracle.s_set(0, 16, B)
+        ref = oracle.match(img, B, 2, kept_o, np.stack([pick["x"], pick["y"]], 1), sp, q,
+                           n_threads=8)
+        np.testing.assert_array_equal(pick["e_num"], ref["e_num"])
+        np.testing.assert_array_equal(G.keys_of(pick, len(sp)), ref["key"])
+    dec = code.decode(0)
+    assert oracle.psnr(img, dec) > 25.0
+    code.free()
