@@ -149,7 +149,7 @@ ENC_CASES = [
     (96, 96, 21, 1, dict()),
     (64, 96, 22, 1, dict(s_mode=1, grid_samples=16)),
     (64, 64, 23, 0, dict(range_size0=8, n_levels=3, domain_step=1)),
-    (128, 128, 1, 0, dict(range_size0=8, single_level=1, domain_step=4, s_mode=1,
+    (128, 128, 1, 0, dict(range_size0=8, n_levels=1, single_level=1, domain_step=4, s_mode=1,
                           grid_samples=16)),
     (48, 80, 24, 1, dict(entropy_percentile=0.75, rms_threshold=5.0)),
     (64, 64, 25, 1, dict(range_size0=4, n_levels=2, domain_step=2, rms_threshold=3.0)),
