@@ -250,6 +250,17 @@ struct fic_matches {
 // ---------------------------------------------------------------- level driver
 namespace {
 
+// An event record that survives stream capture: inside a capture a plain
+// record only orders the captured work, an external record becomes an
+// event-record node of the graph that is recorded at every replay.
+cudaError_t record_event(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return cudaGetLastError();
+  if (cs == cudaStreamCaptureStatusActive)
+    return cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  return cudaEventRecord(e, st);
+}
+
 int level_alloc(fic_ctx* ctx, LevelWs& w, const std::vector<fic_image>& ims, int B, int64_t cap,
                 const fic_params& prm) {
   const int ni = (int)ims.size();
@@ -332,10 +343,10 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
   a.meta = w.meta.as<PlanMeta>();
   a.part = w.part.as<Cand>();
   a.status = ctx->status.as<uint32_t>();
-  if (ev) FIC_CUDA_TRY(cudaEventRecord(ev[1], st));
+  if (ev) FIC_CUDA_TRY(record_event(ev[1], st));
   rc = tc ? launch_match_tc(a, grid, st) : launch_match_f32(a, grid, st);
   if (rc) return rc;
-  if (ev) FIC_CUDA_TRY(cudaEventRecord(ev[2], st));
+  if (ev) FIC_CUDA_TRY(record_event(ev[2], st));
   return launch_reduce_final(w.B, pl.img.as<ImgDev>(), w.rec.as<RangeRec>(), w.n_act.as<int64_t>(),
                              w.cap, w.act_off.as<int64_t>(), pl.slot_off.as<int64_t>(), ni, pl.L,
                              pl.sel.as<SelState>(), w.item_off.as<int64_t>(),
@@ -380,7 +391,7 @@ int encode_device(fic_code* c, cudaStream_t st) {
   for (int l = 0; l < c->n_levels; ++l) {
     LevelWs& w = c->lv[l];
     PoolLevel& pl = w.pool;
-    if (c->profile) FIC_CUDA_TRY(cudaEventRecord(c->ev[l][0], st));
+    if (c->profile) FIC_CUDA_TRY(record_event(c->ev[l][0], st));
     if (l == 0) {
       const int64_t nr = c->h_rng_off[ni];
       const int grid = (int)std::min<int64_t>(65535, ceil_div64(std::max<int64_t>(nr, 1), 256));
@@ -401,7 +412,7 @@ int encode_device(fic_code* c, cudaStream_t st) {
                       nx ? nx->n_act.as<int64_t>() : nullptr,
                       w.scan_scr.as<int32_t>(), w.total.as<int64_t>(), st);
     if (rc) return rc;
-    if (c->profile) FIC_CUDA_TRY(cudaEventRecord(c->ev[l][3], st));
+    if (c->profile) FIC_CUDA_TRY(record_event(c->ev[l][3], st));
   }
   FIC_CUDA_TRY(cudaGetLastError());
   return FIC_OK;

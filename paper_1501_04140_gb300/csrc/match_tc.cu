@@ -323,32 +323,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(MatchArgs a) {
             // fast screen: the chunk's minimum float score (full chunks
             // unmasked; the ragged last chunk masks columns >= nvc)
             auto screen = [&](auto masked) {
-              float mn = INFINITY;
-#pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const float4 f = Df[cc * 32 + j];
-                const float y = fmaf(-w, f.x, c[j]);
+              // two columns per step, four independent running minima
+              float mn[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+              auto score1 = [&](int j, float y, const float4& f) {
                 float s;
                 if constexpr (MODE == MODE_GRID) {
                   float p = rintf(y * f.z);
                   p = fminf(fmaxf(p, 0.f), qf);
                   s = p * fmaf(p, f.y, -y);
-                  if constexpr (decltype(masked)::value) s = j < nvc ? s : INFINITY;
-                  mn = fminf(mn, s);
-                } else if constexpr (MODE == MODE_M2) {
-                  float s0 = fmaf(-p0f, y, f.y), s1 = fmaf(-p1f, y, f.z);
-                  if constexpr (decltype(masked)::value) {
-                    s0 = j < nvc ? s0 : INFINITY;
-                    s1 = j < nvc ? s1 : INFINITY;
-                  }
-                  mn = ptx::fmin3(mn, s0, s1);
                 } else {
                   s = fmaf(-p0f, y, f.y);
-                  if constexpr (decltype(masked)::value) s = j < nvc ? s : INFINITY;
-                  mn = fminf(mn, s);
+                }
+                if constexpr (decltype(masked)::value) s = j < nvc ? s : INFINITY;
+                return s;
+              };
+#pragma unroll
+              for (int j = 0; j < 32; j += 2) {
+                const float4 fa = Df[cc * 32 + j], fb = Df[cc * 32 + j + 1];
+                const float ya = fmaf(-w, fa.x, c[j]), yb = fmaf(-w, fb.x, c[j + 1]);
+                float& m = mn[(j >> 1) & 3];
+                if constexpr (MODE == MODE_M2) {
+                  float a0 = fmaf(-p0f, ya, fa.y), a1 = fmaf(-p1f, ya, fa.z);
+                  float b0 = fmaf(-p0f, yb, fb.y), b1 = fmaf(-p1f, yb, fb.z);
+                  if constexpr (decltype(masked)::value) {
+                    a0 = j < nvc ? a0 : INFINITY;
+                    a1 = j < nvc ? a1 : INFINITY;
+                    b0 = j + 1 < nvc ? b0 : INFINITY;
+                    b1 = j + 1 < nvc ? b1 : INFINITY;
+                  }
+                  m = ptx::fmin3(ptx::fmin3(a0, a1, b0), b1, m);
+                } else {
+                  m = ptx::fmin3(score1(j, ya, fa), score1(j + 1, yb, fb), m);
                 }
               }
-              return mn;
+              return fminf(fminf(mn[0], mn[1]), fminf(mn[2], mn[3]));
             };
             const float mn = nvc >= 32 ? screen(std::false_type{}) : screen(std::true_type{});
             if (__any_sync(0xffffffffu, mn <= best.thr)) {

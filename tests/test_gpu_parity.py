@@ -320,3 +320,29 @@ def test_paper_scale_sampled_parity():
     dec = code.decode(0)
     assert oracle.psnr(img, dec) > 25.0
     code.free()
+
+
+def test_graph_replay_and_profiling():
+    """fic_encode_again on a stream captures the encode once and replays it:
+    same maps as the direct encode; the level timers report positive times."""
+    fic = _fic()
+    torch = G.torch_cuda()
+    ctx = G.ctx()
+    img = synth_image(96, 64, 60, n_textured=1)
+    d = G.dev(img)
+    p = fic.default_params()
+    ref = ctx.encode(d, p)
+    want = ref.transforms(0)
+    ref.free()
+    st = torch.cuda.Stream()
+    code = ctx.encode(d, p, stream=st)
+    code.set_profiling(True)
+    for _ in range(3):
+        ctx.encode_again(code, d, p, stream=st)
+        torch.cuda.synchronize()
+        got = code.transforms(0)
+        np.testing.assert_array_equal(got, want)
+        prof = code.profile()
+        assert len(prof) == 4 and all(m > 0 and lv >= m for m, lv in prof), prof
+    assert code.graph_kernels() > 20
+    code.free()
