@@ -238,6 +238,38 @@ int fic_code_graph_kernels(const fic_code* code, int64_t* n_kernels);
 int fic_decode(fic_ctx* ctx, const fic_code* code, int image_idx, int max_iters, double tol,
                uint8_t* out, int out_pitch, int out_host, void* stream, int* iters_done);
 
+/* Decoder that allocates no device memory.  The paper has no counterpart:
+ * this is a deployment variant of fic_decode for callers that must not let a
+ * library call cudaMalloc -- processes whose device memory belongs to another
+ * allocator (a framework's caching allocator, a pool sized at start-up) and
+ * loops where an allocation's device synchronisation is not acceptable.
+ *
+ * It runs fic_decode's kernels (same iteration, same result) on a workspace
+ * that is a static __device__ array inside this library, sized for at most
+ * FIC_DECODE_STATIC_MAX_PIXELS pixels (width * height) and
+ * FIC_DECODE_STATIC_MAX_ITERS iterations: about 20 MiB that every GPU which
+ * loads the library holds until the process exits.
+ *
+ *   codes      n_codes maps in DEVICE memory, caller-owned (for example the
+ *              output of fic_code_get copied to the device); every block must
+ *              lie inside the image, sizes 2/4/8/16, iso 0..7, q > 0
+ *              (FIC_EINVAL otherwise, checked on the device before decoding)
+ *   out        width x height bytes at out_pitch, DEVICE memory, caller-owned
+ *   iters_done iterations run (may be NULL)
+ *
+ * Returns FIC_EINVAL for sizes or iteration counts above the maximum.  The
+ * first call on a device looks up the array's device address (and loads the
+ * library's device code if that has not happened yet), so make it before any
+ * stream capture.  Every call uses the same array and leaves its contents
+ * behind; the call resets what must start from zero.  Calls whose GPU work
+ * overlaps (on different streams or threads) race on the array: serialise
+ * them.  Enqueues on `stream` and synchronises it before returning. */
+#define FIC_DECODE_STATIC_MAX_PIXELS (1024 * 1024)
+#define FIC_DECODE_STATIC_MAX_ITERS 1024
+int fic_decode_static(const fic_transform* codes, int64_t n_codes, int width, int height,
+                      int max_iters, double tol, uint8_t* out, int out_pitch, void* stream,
+                      int* iters_done);
+
 #ifdef __cplusplus
 }
 #endif

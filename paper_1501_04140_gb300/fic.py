@@ -106,6 +106,8 @@ _SIGS = {
     "fic_code_graph_kernels": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "fic_decode": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_double, _P, C.c_int, C.c_int, _P,
                              C.POINTER(C.c_int)]),
+    "fic_decode_static": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_double, _P,
+                                    C.c_int, _P, C.POINTER(C.c_int)]),
 }
 
 _lib = None
@@ -189,6 +191,19 @@ def _stream_ptr(stream):
     if hasattr(stream, "cuda_stream"):
         return stream.cuda_stream
     return int(stream)
+
+
+def decode_static(codes_dev, n_codes: int, width: int, height: int, out_dev, out_pitch: int,
+                  max_iters: int = 300, tol: float = 1e-7, stream=None) -> int:
+    """fic_decode_static: decode `n_codes` maps held in device memory at
+    `codes_dev` (a pointer or a CUDA tensor) into the device buffer `out_dev`
+    without any device allocation.  Returns the iteration count."""
+    it = C.c_int()
+    cp = codes_dev.data_ptr() if hasattr(codes_dev, "data_ptr") else codes_dev
+    op = out_dev.data_ptr() if hasattr(out_dev, "data_ptr") else out_dev
+    _check(load().fic_decode_static(cp, n_codes, width, height, max_iters, tol, op, out_pitch,
+                                    _stream_ptr(stream), C.byref(it)), "fic_decode_static")
+    return it.value
 
 
 class Context:
