@@ -56,7 +56,7 @@ struct LevelWs {
   PoolLevel pool;
   DevBuf img;                              // ImgDev per image (px, py of this level)
   int64_t cap = 0;                         // ranges capacity
-  DevBuf rec, n_act, act_off, act_cnt, mom, apack, a32, res, acc, codes;
+  DevBuf rec, n_act, act_off, act_cnt, mom, gthr, apack, a32, res, acc, codes;
   DevBuf acc_cnt, rej_cnt, code_off;
   DevBuf item_off, chunks, meta, part;
   int64_t item_cap = 0, mt_cap = 0;
@@ -64,8 +64,8 @@ struct LevelWs {
   void release_all() {
     DevBuf* all[] = {&pool.off,  &pool.img,   &pool.keys,   &pool.sd,    &pool.sq,     &pool.sel,
                      &pool.hist, &pool.kept,  &pool.bpack,  &pool.b32,   &pool.dom,    &pool.domf,
-                     &pool.scan_scratch, &pool.total, &pool.slot_off, &img, &rec, &n_act, &act_off,
-                     &act_cnt,   &mom,        &apack,       &a32,        &res,         &acc,
+                     &pool.scan_scratch, &pool.total, &pool.slot_off, &pool.umax, &img, &rec, &n_act, &act_off,
+                     &act_cnt,   &mom,        &gthr,        &apack,       &a32,        &res,         &acc,
                      &codes,     &acc_cnt,    &rej_cnt,     &code_off,   &item_off,    &chunks,
                      &meta,      &part,       &scan_scr,    &total};
     for (DevBuf* b : all) b->release();
@@ -112,6 +112,7 @@ int pool_alloc(PoolLevel& pl) {
   rc |= pl.kept.reserve(sizeof(int32_t) * S);
   rc |= pl.dom.reserve(sizeof(DomRec) * S);
   rc |= pl.domf.reserve(sizeof(float4) * S);
+  rc |= pl.umax.reserve(16);
   if (pl.want_tc) rc |= pl.bpack.reserve(sizeof(uint16_t) * S * pl.Kp);
   if (pl.want_f32) rc |= pl.b32.reserve(sizeof(float) * S * pl.n);
   rc |= pl.scan_scratch.reserve(sizeof(int32_t) * scan_scratch_blocks(P));
@@ -276,6 +277,7 @@ int level_alloc(fic_ctx* ctx, LevelWs& w, const std::vector<fic_image>& ims, int
   rc |= w.act_off.reserve(sizeof(int64_t) * (ni + 1));
   rc |= w.act_cnt.reserve(sizeof(int64_t) * ni);
   rc |= w.mom.reserve(sizeof(RangeMom) * C);
+  rc |= w.gthr.reserve(sizeof(uint32_t) * C);
   if (tc) rc |= w.apack.reserve(sizeof(uint16_t) * C * 8 * w.Kp);
   else rc |= w.a32.reserve(sizeof(float) * C * 8 * w.n);
   rc |= w.res.reserve(sizeof(fic_transform) * C);
@@ -312,7 +314,7 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
   const int ni = pl.n_images;
   const bool tc = prm.precision == FIC_PREC_TENSOR;
   int rc = launch_range_pack(w.B, pl.img.as<ImgDev>(), w.rec.as<RangeRec>(), w.n_act.as<int64_t>(),
-                             w.cap, w.Kp, w.mom.as<RangeMom>(),
+                             w.cap, w.Kp, w.mom.as<RangeMom>(), w.gthr.as<uint32_t>(),
                              tc ? w.apack.as<uint16_t>() : nullptr,
                              tc ? nullptr : w.a32.as<float>(), st);
   if (rc) return rc;
@@ -333,7 +335,9 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
   a.bpack = pl.bpack.as<uint16_t>();
   a.b32 = pl.b32.as<float>();
   a.dom = pl.dom.as<DomRec>();
-  a.domf = pl.domf.as<float4>();
+  a.domf = pl.domf.as<float>();
+  a.gthr = w.gthr.as<uint32_t>();
+  a.umax = pl.umax.as<float>();
   a.act_off = w.act_off.as<int64_t>();
   a.act_cnt = w.act_cnt.as<int64_t>();
   a.pool_off = pl.slot_off.as<int64_t>();
@@ -655,7 +659,7 @@ void fic_pool_free(fic_pool* p) {
   PoolLevel& pl = p->pl;
   DevBuf* all[] = {&pl.off,  &pl.slot_off, &pl.img, &pl.keys, &pl.sd,   &pl.sq,   &pl.sel,
                    &pl.hist, &pl.kept,     &pl.bpack, &pl.b32, &pl.dom, &pl.domf, &pl.scan_scratch,
-                   &pl.total};
+                   &pl.total, &pl.umax};
   for (DevBuf* b : all) b->release();
   p->staging.buf.release();
   delete p;
@@ -703,6 +707,7 @@ int fic_match_level(fic_ctx* ctx, const fic_image* img, const fic_pool* pool,
     w.pool.img = src.img; w.pool.sel = src.sel; w.pool.slot_off = src.slot_off;
     w.pool.bpack = src.bpack; w.pool.b32 = src.b32; w.pool.dom = src.dom;
     w.pool.domf = src.domf;
+    w.pool.umax = src.umax;
     std::vector<RangeRec> rec(n_ranges);
     for (int r = 0; r < n_ranges; ++r) rec[r] = RangeRec{0, range_xy[2 * r], range_xy[2 * r + 1], -1};
     const int64_t nact = n_ranges, off[2] = {0, n_ranges};
@@ -720,6 +725,7 @@ int fic_match_level(fic_ctx* ctx, const fic_image* img, const fic_pool* pool,
   // drop the borrowed buffers before any release
   w.pool.img = DevBuf(); w.pool.sel = DevBuf(); w.pool.slot_off = DevBuf();
   w.pool.bpack = DevBuf(); w.pool.b32 = DevBuf(); w.pool.dom = DevBuf(); w.pool.domf = DevBuf();
+  w.pool.umax = DevBuf();
   if (rc) {
     fic_matches_free(m);
     return rc;

@@ -46,6 +46,8 @@ struct RangeMom {
   int32_t sr;      // sum of r
   int32_t srp;     // sum of (r - 128)
   int64_t a;       // n sum r^2 - (sum r)^2
+  int32_t sabs;    // sum of |r - 128|: bounds the range's correlations
+  int32_t pad;
 };
 
 // Per kept domain, for the scoring epilogues.

@@ -50,7 +50,7 @@ struct PoolLevel {
   int nsm = 0;                       // SMs of the device (grid sizing)
   // per position: off, keys, sd, sq; per slot: slot_off, kept, bpack, b32, dom, domf
   DevBuf off, slot_off, img, keys, sd, sq, sel, hist, kept, bpack, b32, dom, domf, scan_scratch,
-      total;
+      total, umax;
 };
 
 // Launchers (pool.cu)

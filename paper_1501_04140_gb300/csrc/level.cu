@@ -32,59 +32,77 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(int32_t* cnt, int nb, int6
 }
 
 // ---------------------------------------------------------------- range operand
+// One thread per range pixel (256 / n ranges per block): the pixel r goes to
+// its place in each of the 8 rows T_k^-1(R) (<T_k^-1 R, D> = <R, T_k D>), and
+// the block reduces the range's moments in shared memory.  Also resets the
+// range's screening threshold for the matcher.
+constexpr int kRangePackThreads = 256;
+
 template <int B>
-__global__ void k_range_pack(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec,
-                             const int64_t* __restrict__ n_act, int Kp,
-                             RangeMom* __restrict__ mom, uint16_t* __restrict__ apack,
-                             float* __restrict__ a32) {
+__global__ void __launch_bounds__(kRangePackThreads)
+k_range_pack(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec,
+             const int64_t* __restrict__ n_act, int Kp, RangeMom* __restrict__ mom,
+             uint32_t* __restrict__ gthr, uint16_t* __restrict__ apack,
+             float* __restrict__ a32) {
   constexpr int n = B * B;
+  constexpr int RPB = kRangePackThreads / n;  // ranges per block step
+  __shared__ int s_sr[RPB], s_s2[RPB], s_sa[RPB];
   const int64_t N = *n_act;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    const RangeRec r = rec[g];
-    const ImgDev I = imgs[r.img];
-    const uint8_t* base = I.pix + (int64_t)r.y * I.pitch + r.x;
-    int sr = 0;
-    int64_t s2 = 0;
-    for (int i = 0; i < B; ++i)
-      for (int j = 0; j < B; ++j) {
-        const int v = base[(int64_t)i * I.pitch + j];
-        sr += v;
-        s2 += v * v;
-        // row k holds T_k^-1(R): <T_k^-1 R, D> = <R, T_k D>
-        for (int k = 0; k < 8; ++k) {
-          int si, sj;
-          iso_src(B, k, i, j, &si, &sj);
-          const int e = si * B + sj;
-          if (apack) {
-            const int64_t idx = (((g * (Kp >> 3)) + (e >> 3)) * 8 + k) * 8 + (e & 7);
-            apack[idx] = __half_as_ushort(__int2half_rn(v - 128));
-          }
-          if (a32) a32[(g * 8 + k) * n + e] = (float)(v - 128);
-        }
+  const int lr = threadIdx.x / n, e = threadIdx.x % n;
+  const int i = e / B, j = e % B;
+  for (int64_t g0 = (int64_t)blockIdx.x * RPB; g0 < N; g0 += (int64_t)gridDim.x * RPB) {
+    if (threadIdx.x < RPB) s_sr[threadIdx.x] = 0, s_s2[threadIdx.x] = 0, s_sa[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t g = g0 + lr;
+    if (g < N) {
+      const RangeRec r = rec[g];
+      const ImgDev I = imgs[r.img];
+      const int v = I.pix[(int64_t)(r.y + i) * I.pitch + r.x + j];
+      atomicAdd(&s_sr[lr], v);
+      atomicAdd(&s_s2[lr], v * v);  // <= 256 * 255^2 < 2^31
+      atomicAdd(&s_sa[lr], v >= 128 ? v - 128 : 128 - v);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        int si, sj;
+        iso_src(B, k, i, j, &si, &sj);
+        const int d = si * B + sj;
+        if (apack)
+          apack[(((g * (Kp >> 3)) + (d >> 3)) * 8 + k) * 8 + (d & 7)] =
+              __half_as_ushort(__int2half_rn(v - 128));
+        if (a32) a32[(g * 8 + k) * n + d] = (float)(v - 128);
       }
-    if (apack && n < Kp)
-      for (int e = n; e < Kp; ++e)
-        for (int k = 0; k < 8; ++k) apack[(((g * (Kp >> 3)) + (e >> 3)) * 8 + k) * 8 + (e & 7)] = 0;
-    RangeMom m;
-    m.sr = sr;
-    m.srp = sr - 128 * n;
-    m.a = (int64_t)n * s2 - (int64_t)sr * sr;
-    mom[g] = m;
+      if (apack)  // zero the K padding (B = 2: K = 4 of 16)
+        for (int d = n + e; d < Kp; d += n)
+#pragma unroll
+          for (int k = 0; k < 8; ++k) apack[(((g * (Kp >> 3)) + (d >> 3)) * 8 + k) * 8 + (d & 7)] = 0;
+    }
+    __syncthreads();
+    if (g < N && e == 0) {
+      const int sr = s_sr[lr];
+      RangeMom m;
+      m.sr = sr;
+      m.srp = sr - 128 * n;
+      m.a = (int64_t)n * s_s2[lr] - (int64_t)sr * sr;
+      m.sabs = s_sa[lr];
+      m.pad = 0;
+      mom[g] = m;
+      if (gthr) gthr[g] = kThrInit;
+    }
   }
 }
 
 int launch_range_pack(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
-                      int64_t cap, int Kp, RangeMom* mom, uint16_t* apack, float* a32,
-                      cudaStream_t st) {
-  const int threads = 128;
-  int grid = (int)ceil_div64(cap > 0 ? cap : 1, threads);
+                      int64_t cap, int Kp, RangeMom* mom, uint32_t* gthr, uint16_t* apack,
+                      float* a32, cudaStream_t st) {
+  const int threads = kRangePackThreads;
+  const int64_t rpb = threads / (B * B);
+  int grid = (int)ceil_div64(cap > 0 ? cap : 1, rpb);
   if (grid > 65535) grid = 65535;
   switch (B) {
-    case 16: k_range_pack<16><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, apack, a32); break;
-    case 8: k_range_pack<8><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, apack, a32); break;
-    case 4: k_range_pack<4><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, apack, a32); break;
-    case 2: k_range_pack<2><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, apack, a32); break;
+    case 16: k_range_pack<16><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, gthr, apack, a32); break;
+    case 8: k_range_pack<8><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, gthr, apack, a32); break;
+    case 4: k_range_pack<4><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, gthr, apack, a32); break;
+    case 2: k_range_pack<2><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, gthr, apack, a32); break;
     default: return FIC_EINVAL;
   }
   return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;

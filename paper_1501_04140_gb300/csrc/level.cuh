@@ -22,7 +22,11 @@ struct MatchArgs {
   const uint16_t* bpack;            // f16 domains, core-matrix layout
   const float* b32;                 // fp32 domains
   const DomRec* dom;                // per domain slot
-  const float4* domf;               // per domain slot: {SD', u0, u1 | g, 0}
+  const float* domf;                // per 128-slot tile: planes {SD'}, {F0}, {F1}, {0}
+  const float* umax;                // largest V / (8 q n) of the level's kept domains
+  uint32_t* gthr;                   // per range: best screening threshold found so far
+                                    // (order-preserving bits of a float), shared by
+                                    // every CTA that scores the range
   const int64_t* act_off;           // n_images + 1 (ranges)
   const int64_t* act_cnt;           // n_images
   const int64_t* pool_off;          // n_images + 1 (domain slots)
@@ -35,8 +39,19 @@ struct MatchArgs {
 };
 
 int launch_range_pack(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
-                      int64_t cap, int Kp, RangeMom* mom, uint16_t* apack, float* a32,
-                      cudaStream_t st);
+                      int64_t cap, int Kp, RangeMom* mom, uint32_t* gthr, uint16_t* apack,
+                      float* a32, cudaStream_t st);
+
+// Screening thresholds are shared between CTAs as order-preserving unsigned
+// images of floats (atomicMin on the image = min on the float).
+constexpr uint32_t kThrInit = 0xFF800000u;  // image of +inf
+__device__ inline uint32_t thr_to_ord(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ inline float ord_to_thr(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
 
 __global__ void k_plan(int n_images, const int64_t* act_off, const int64_t* act_cnt,
                        const SelState* sel, int target_items, int64_t item_cap, int64_t mt_cap,

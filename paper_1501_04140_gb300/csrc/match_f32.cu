@@ -76,7 +76,8 @@ k_match_f32(MatchArgs a) {
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
       __syncthreads();
       for (int j = tid; j < kTileDoms; j += blockDim.x) {
-        Df[j] = a.domf[d0 + j];
+        const float* ft = a.domf + (d0 >> 7) * (4 * kTileDoms) + j;  // d0: tile start
+        Df[j] = make_float4(ft[0], ft[kTileDoms], ft[2 * kTileDoms], ft[3 * kTileDoms]);
         Dpos[j] = a.dom[d0 + j].pos;
       }
       for (int k0 = 0; k0 < n; k0 += KC) {

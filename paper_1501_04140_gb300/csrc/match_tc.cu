@@ -13,11 +13,14 @@
 // Warp roles of one persistent CTA per SM:
 //   warp 0      producer: bulk copies (TMA engine) of the resident 128-row
 //               range tile, the streamed 128-domain tiles (one stage per K
-//               half at B = 16) and the per-domain scoring records;
+//               half at B = 16) and each tile's per-domain scoring planes
+//               and exact records;
 //   warp 1      allocates tensor memory and issues the MMAs (one thread);
-//   warps 2-5   epilogue: each owns 32 TMEM lanes = 32 rows (range, isometry)
-//               and reduces the 128 columns of every tile to the row's best
-//               (domain, s) candidate.
+//   warps 2-3   idle (they complete the control warpgroup);
+//   warps 4-    epilogue, EG groups of four warps (EG = 3, or 2 at B = 16
+//               where shared memory is short): each warp owns the 32 TMEM
+//               lanes = 32 rows (range, isometry) of its quarter; the groups
+//               take turns on the tiles and merge their row bests per item.
 //
 // Epilogue.  For s = p/q, E of Eq. 1 with o from Eq. 3 is, up to the
 // range-only term, E' = p^2 V - 8 p q C with C = n <r', Ds'> - sum r' sum Ds'
@@ -27,7 +30,30 @@
 // row's best exact score by more than the level's rounding bound `delta`;
 // every other candidate is scored exactly in int64 and compared with the
 // tie-break key (pos * 8 + k) * |S| + s_idx.  The result therefore equals the
-// exhaustive exact argmin.
+// exhaustive exact argmin.  A threshold only has to bound the exact score of
+// some candidate of the same range that stays in the reduction, so the 8
+// isometry rows of a range share theirs (warp shuffles) and every CTA that
+// scores the range shares it through a per-range word in global memory
+// (atomicMin on an order-preserving image of the float).  Scores of two
+// columns at a time use the packed f32x2 FMA.
+//
+// Rounding bound.  corr is exact, w = sum r' / n is exact (n is a power of
+// two) and the FMAs round once each, so y carries at most 2^-24 |y| and a
+// score F - p y (F = p^2 u rounded from double) at most
+//     2^-23 (F + p |y|) <= 2^-23 (p^2 umax + p Y),   Y = 1024 sum |r'|,
+// because |corr| <= 512 sum |r'| and |w sum Ds'| <= 512 |sum r'|; umax is the
+// largest u of the level's kept domains.  The kernel uses 4x that bound
+// (`delta`), per range.  A chunk's best float candidate X is scored exactly,
+// so any candidate whose float score exceeds X's by more than 2 delta is
+// strictly worse than X and is skipped as well.
+//
+// Grid S (s = p / q, p = 0..q).  E'(p) = V (p - p*)^2 + const with the real
+// minimiser p* = 4 q C / V, so the best grid point is the nearest integer to
+// p* clamped to [0, q].  The float path takes p^ = clamp(rint(y 4qn / V)); p^
+// can miss the exact choice by one only when p* lies within about 2^-22 q of
+// a half-integer, where the two neighbours' scores differ by at most
+// 2^-21 q umax -- inside the level-wide margin used on the grid (2^-20 times
+// the worst-case score bound) -- and the exact pass scores p^ - 1, p^, p^ + 1.
 #include <math.h>
 
 #include <type_traits>
@@ -37,8 +63,28 @@
 
 namespace fic {
 
+constexpr int kCtlWarps = 4;  // producer, MMA issuer and two idle warps: one warpgroup
+
+// Epilogue warpgroups and registers.  The block launches with LREGS per
+// thread (what 65536 registers give its threads); the control warpgroup
+// hands most of its share to the epilogue warpgroups (setmaxnreg).  The host
+// checks the launch count before the first launch: an increment that the
+// block's total cannot pay for would never complete.
+template <int EG>
+struct TcWarps {
+  static constexpr int EPI_WARPS = 4 * EG;  // EG warps per TMEM lane quarter
+  static constexpr int THREADS = 32 * (kCtlWarps + EPI_WARPS);
+  static constexpr int LREGS = EG == 2 ? 168 : 128;
+  static constexpr int CREGS = EG == 2 ? 40 : 32;
+  static constexpr int EREGS = EG == 2 ? 232 : 160;
+  static_assert(32 * (kCtlWarps * CREGS + EPI_WARPS * EREGS) <= THREADS * LREGS,
+                "register split exceeds the launch budget");
+};
+
 template <int B>
 struct TcCfg {
+  static constexpr int EG = B == 16 ? 2 : 3;          // epilogue warp groups
+  using Wp = TcWarps<EG>;
   static constexpr int n = B * B;
   static constexpr int Kp = n < 16 ? 16 : n;          // K padded to the MMA K step
   static constexpr int NKC = n > 128 ? n / 128 : 1;   // exact accumulators per tile
@@ -46,25 +92,31 @@ struct TcCfg {
   static constexpr int KSTEPS = KS / 16;              // MMAs per stage
   static constexpr int A_BYTES = kTileRows * Kp * 2;
   static constexpr int ST_BYTES = kTileDoms * KS * 2;
-  static constexpr int NST = B == 16 ? 4 : 8;
-  static constexpr int NACC = B == 16 ? 2 : 4;
+  static constexpr int NST = B == 16 ? 4 : B == 8 ? 6 : 8;   // operand stages
+  static constexpr int NACC = B == 16 ? 2 : 4;                // TMEM accumulators
+  static constexpr int ND = B == 16 ? 4 : B == 8 ? 8 : 16;    // scoring-record stages
   static constexpr int TCOLS = 512;
-  static constexpr int DF_BYTES = kTileDoms * 16;
-  static constexpr int SCR_BYTES = 4 * 32 * 32 * 4;
+  static constexpr int CW = NKC == 1 ? 32 : 16;       // tile columns per epilogue chunk
+  static constexpr int NCH = kTileDoms / CW;
+  static constexpr int DT_BYTES = 4 * kTileDoms * 4;  // float planes {sum Ds', F0, F1, 0}
+  static constexpr int DR_BYTES = kTileDoms * 16;     // DomRec per column
+  static constexpr int D_BYTES = DT_BYTES + DR_BYTES;
+  static constexpr int MRG_BYTES = (EG - 1) * kTileRows * 16;
+  static constexpr int SCR_BYTES = Wp::EPI_WARPS * 32 * CW * 4;
   static constexpr int OFF_B = A_BYTES;
-  static constexpr int OFF_DF = OFF_B + NST * ST_BYTES;
-  static constexpr int OFF_SCR = OFF_DF + NACC * DF_BYTES;
+  static constexpr int OFF_D = OFF_B + NST * ST_BYTES;
+  static constexpr int OFF_MRG = OFF_D + ND * D_BYTES;
+  static constexpr int OFF_SCR = OFF_MRG + MRG_BYTES;
   static constexpr int OFF_BAR = OFF_SCR + SCR_BYTES;
-  static constexpr int NBAR = 2 * NST + 2 + 3 * NACC + 1;
+  static constexpr int NBAR = 2 * NST + 2 + 2 * NACC + 2 * ND + 1;
   static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
   static constexpr int BYTES = OFF_MISC + 16;
   // one CTA per SM: the CTA owns all 512 TMEM columns
   static constexpr int SMEM = BYTES < 120 * 1024 ? 120 * 1024 : BYTES;
   static_assert(NACC * NKC * 128 <= TCOLS, "tensor memory");
-  static_assert(BYTES + 1024 <= 227 * 1024, "shared memory");
+  static_assert(BYTES + 128 <= 227 * 1024, "shared memory");
 };
 
-constexpr int kTcThreads = 192;
 constexpr int MODE_M1 = 0, MODE_M2 = 1, MODE_GRID = 2;
 
 struct ItemGeo {
@@ -89,28 +141,22 @@ __device__ inline ItemGeo item_geo(const MatchArgs& a, int64_t it, int CH) {
   return g;
 }
 
-// Per-row best candidate of the epilogue.
-struct RowBest {
-  int64_t e;    // exact E'
-  int64_t key;
-  float thr;    // skip a candidate whose float score is above this
-};
-
+// Skip a candidate whose float score is above this (exact E' plus the margin).
 __device__ inline float thr_of(int64_t e, double inv8qn, float delta) {
   return __double2float_ru(fma((double)e, inv8qn, (double)delta));
 }
 
 template <int B, int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(MatchArgs a) {
+__global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs a) {
   using Cf = TcCfg<B>;
-  constexpr int n = Cf::n;
+  constexpr int EG = Cf::EG;
+  constexpr int n = B * B;
   constexpr int LOGN = B == 16 ? 8 : B == 8 ? 6 : B == 4 ? 4 : 2;
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int CW = Cf::CW;
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   uint8_t* sA = smem;
   uint8_t* sB = smem + Cf::OFF_B;
-  float4* sDf = (float4*)(smem + Cf::OFF_DF);
-  float* sScr = (float*)(smem + Cf::OFF_SCR);
   uint64_t* bars = (uint64_t*)(smem + Cf::OFF_BAR);
   uint64_t* full_b = bars;
   uint64_t* empty_b = bars + Cf::NST;
@@ -118,8 +164,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(MatchArgs a) {
   uint64_t* a_empty = a_full + 1;
   uint64_t* acc_full = a_empty + 1;
   uint64_t* acc_empty = acc_full + Cf::NACC;
-  uint64_t* df_full = acc_empty + Cf::NACC;
-  uint64_t* done_bar = df_full + Cf::NACC;
+  uint64_t* d_full = acc_empty + Cf::NACC;
+  uint64_t* d_empty = d_full + Cf::ND;
+  uint64_t* done_bar = d_empty + Cf::ND;
   uint32_t* tmem_slot = (uint32_t*)(smem + Cf::OFF_MISC);
   volatile int* abort_flag = (volatile int*)(smem + Cf::OFF_MISC + 4);
 
@@ -133,8 +180,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(MatchArgs a) {
     ptx::mbar_init(a_empty, 1);
     for (int i = 0; i < Cf::NACC; ++i) {
       ptx::mbar_init(&acc_full[i], 1);
-      ptx::mbar_init(&acc_empty[i], 4);
-      ptx::mbar_init(&df_full[i], 1);
+      ptx::mbar_init(&acc_empty[i], 4);  // the four warps of the group that reads it
+    }
+    for (int i = 0; i < Cf::ND; ++i) {
+      ptx::mbar_init(&d_full[i], 1);
+      ptx::mbar_init(&d_empty[i], 4);
     }
     ptx::mbar_init(done_bar, 1);
     *abort_flag = 0;
@@ -156,13 +206,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(MatchArgs a) {
     atomicOr(a.status, kStatusTimeout);
   };
 
+  if (warp < kCtlWarps) {
+  ptx::setmaxnreg_dec<Cf::Wp::CREGS>();
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       uint32_t bi = 0, ai = 0, ti = 0;
-      uint32_t issued_par[Cf::NST];
-      bool issued[Cf::NST];
+      uint32_t issued_par[Cf::NST], d_par[Cf::ND];
+      bool issued[Cf::NST], d_issued[Cf::ND];
       for (int i = 0; i < Cf::NST; ++i) issued[i] = false, issued_par[i] = 0;
+      for (int i = 0; i < Cf::ND; ++i) d_issued[i] = false, d_par[i] = 0;
       bool ok = true;
       for (int64_t it = blockIdx.x; ok && it < items; it += gridDim.x) {
         const ItemGeo g = item_geo(a, it, CH);
@@ -171,16 +224,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(MatchArgs a) {
         ptx::bulk_g2s(sA, a.apack + g.r0 * 8 * Cf::Kp, Cf::A_BYTES, a_full);
         ++ai;
         for (int t = g.t0; ok && t < g.t1; ++t) {
-          const int db = ti % Cf::NACC;
-          if (!ptx::mbar_wait(&acc_empty[db], ((ti / Cf::NACC) & 1) ^ 1) || *abort_flag) {
+          // the tile's scoring records: a ring of their own, ND tiles ahead
+          const int db = ti % Cf::ND;
+          if (!ptx::mbar_wait(&d_empty[db], ((ti / Cf::ND) & 1) ^ 1) || *abort_flag) {
             ok = false;
             break;
           }
-          ptx::mbar_expect_tx(&df_full[db], Cf::DF_BYTES);
-          ptx::bulk_g2s((uint8_t*)sDf + db * Cf::DF_BYTES,
-                        a.domf + g.slot0 + (int64_t)t * kTileDoms, Cf::DF_BYTES, &df_full[db]);
-          ++ti;
           const int64_t tile_g = g.slot0 / kTileDoms + t;
+          uint8_t* dst = smem + Cf::OFF_D + db * Cf::D_BYTES;
+          ptx::mbar_expect_tx(&d_full[db], Cf::D_BYTES);
+          ptx::bulk_g2s(dst, a.domf + tile_g * (4 * kTileDoms), Cf::DT_BYTES, &d_full[db]);
+          ptx::bulk_g2s(dst + Cf::DT_BYTES, a.dom + tile_g * kTileDoms, Cf::DR_BYTES,
+                        &d_full[db]);
+          d_issued[db] = true;
+          d_par[db] = (ti / Cf::ND) & 1;
+          ++ti;
           for (int kc = 0; kc < Cf::NKC; ++kc) {
             const int st = bi % Cf::NST;
             if (!ptx::mbar_wait(&empty_b[st], ((bi / Cf::NST) & 1) ^ 1) || *abort_flag) {
@@ -201,6 +259,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(MatchArgs a) {
       // drain: every copy this thread issued has landed before the CTA exits
       for (int i = 0; i < Cf::NST; ++i)
         if (issued[i]) ptx::mbar_wait(&full_b[i], issued_par[i]);
+      for (int i = 0; i < Cf::ND; ++i)
+        if (d_issued[i]) ptx::mbar_wait(&d_full[i], d_par[i]);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -248,158 +308,310 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(MatchArgs a) {
       ptx::mma_commit(done_bar);
       if (!ptx::mbar_wait(done_bar, 0)) atomicOr(a.status, kStatusTimeout);
     }
+  }
   } else {
+    ptx::setmaxnreg_inc<Cf::Wp::EREGS>();
     // ------------------------------------------------------------ epilogue
-    const int qd = warp & 3;                 // TMEM lane quarter of this warp
+    // Warps 4..: quarter qd = warp % 4 of the TMEM lanes (rows); group h
+    // takes the tiles ti = h mod EG.  The groups' row bests merge at item end.
+    const int ew = warp - kCtlWarps;
+    const int h = ew >> 2;
+    const int qd = warp & 3;
     const int row = qd * 32 + lane;          // tile row = (range, isometry)
     const int k_iso = row & 7;
-    float* scr = sScr + (warp - 2) * 32 * 32;
+    float* scr = (float*)(smem + Cf::OFF_SCR) + ew * 32 * CW;
+    Cand* mrg = (Cand*)(smem + Cf::OFF_MRG);
     const int m_s = a.S.m;
     const int qv = a.S.q;
     const double inv8qn = 1.0 / (8.0 * qv * n);
-    const float delta = a.delta;
+    const double umax = (double)*a.umax;
+    const double pmx = (double)(MODE == MODE_M2 ? max(a.S.p[0], a.S.p[1]) : a.S.p[0]);
     const float p0f = (float)a.S.p[0], p1f = (float)a.S.p[1];
     const float qf = (float)qv;
+    const float2 np0 = make_float2(-p0f, -p0f), np1 = make_float2(-p1f, -p1f);
     uint32_t ti = 0;
     bool ok = true;
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
       const ItemGeo g = item_geo(a, it, CH);
       const int rr = row >> 3;
       const bool valid = rr < g.nr;
-      int32_t srp = 0;
-      if (valid) srp = a.mom[g.r0 + rr].srp;
+      int32_t srp = 0, sabs = 0;
+      if (valid) {
+        const RangeMom m = a.mom[g.r0 + rr];
+        srp = m.srp;
+        sabs = m.sabs;
+      }
+      // rounding bound of this range's float scores (score units), the same
+      // for its 8 rows in every CTA: 4x the bound derived above
+      const float delta =
+          MODE == MODE_GRID
+              ? a.delta
+              : __double2float_ru(ldexp(pmx * pmx * umax + pmx * 1024.0 * (double)sabs, -21));
       const float w = (float)srp / (float)n;
-      RowBest best{INT64_MAX, INT64_MAX, valid ? INFINITY : -INFINITY};
+      const float2 nw2 = make_float2(-w, -w);
+      uint32_t* gth = a.gthr + (g.r0 + (valid ? rr : 0));
+      uint32_t gpre = valid ? __ldcg(gth) : kThrInit;
+      int64_t best_e = INT64_MAX, best_key = INT64_MAX;
+      float thr = valid ? INFINITY : -INFINITY;
+      bool improved = false;
 
-      // exact score of one candidate (column col of tile t, set index si)
-      auto exact = [&](int t, int col, float cf, int si) {
-        const DomRec d = a.dom[g.slot0 + (int64_t)t * kTileDoms + col];
+      // exact score of one candidate (tile column col, set index si)
+      auto exact = [&](const DomRec* sDom, int col, float cf, int si) {
+        const DomRec d = sDom[col];
         const int64_t ci = (int64_t)(int)cf;
         const int64_t C = (ci << LOGN) - (int64_t)srp * (int64_t)d.sdp;
         const int64_t p = (MODE == MODE_GRID) ? si : a.S.p[si];
         const int64_t e = p * p * d.v - 8 * p * qv * C;
         const int64_t key = ((int64_t)d.pos * 8 + k_iso) * m_s + si;
-        if (e < best.e || (e == best.e && key < best.key)) {
-          best.e = e;
-          best.key = key;
-          best.thr = thr_of(e, inv8qn, delta);
+        if (e < best_e || (e == best_e && key < best_key)) {
+          best_e = e;
+          best_key = key;
+          const float to = thr_of(e, inv8qn, delta);
+          if (to < thr) {
+            thr = to;
+            improved = true;
+          }
         }
       };
 
-      for (int t = g.t0; t < g.t1; ++t) {
+      for (int t = g.t0; t < g.t1; ++t, ++ti) {
+        if ((int)(ti % EG) != h) continue;
         const int ab = ti % Cf::NACC;
-        const uint32_t par = (ti / Cf::NACC) & 1;
-        const bool got =
-            ok && ptx::mbar_wait(&acc_full[ab], par) && ptx::mbar_wait(&df_full[ab], par);
+        const int db = ti % Cf::ND;
+        const bool got = ok && ptx::mbar_wait(&acc_full[ab], (ti / Cf::NACC) & 1) &&
+                         ptx::mbar_wait(&d_full[db], (ti / Cf::ND) & 1);
         // the TMEM loads below are warp-collective: the lanes agree on the outcome
         const bool all = __all_sync(0xffffffffu, got);
         if (ok && !all && lane == 0) fail();
         ok = all;
         ptx::tc_fence_after();
-        const float4* Df = sDf + ab * kTileDoms;
+        // threshold found by any CTA for this range (loaded one tile ahead)
+        if (valid) thr = fminf(thr, ord_to_thr(gpre));
+        gpre = valid ? __ldcg(gth) : kThrInit;
+        const float* sX = (const float*)(smem + Cf::OFF_D + db * Cf::D_BYTES);
+        const float* sF0 = sX + kTileDoms;
+        const float* sF1 = sX + 2 * kTileDoms;
+        const DomRec* sDom = (const DomRec*)(smem + Cf::OFF_D + db * Cf::D_BYTES + Cf::DT_BYTES);
         const int nv = min(kTileDoms, g.nkept - t * kTileDoms);
-        if (ok) {
-#pragma unroll 1
-          for (int cc = 0; cc < 4; ++cc) {
-            const int nvc = nv - cc * 32;
-            if (nvc <= 0) break;
-            uint32_t r0[32];
-            const uint32_t ta = tmem + ((uint32_t)(qd * 32) << 16) +
-                                (uint32_t)(ab * Cf::NKC * kTileDoms + cc * 32);
-            ptx::tmem_ld32(ta, r0);
-            float c[32];
-            if constexpr (Cf::NKC == 2) {
-              uint32_t r1[32];
-              ptx::tmem_ld32(ta + kTileDoms, r1);
-              ptx::tmem_wait(r0);
-              ptx::tmem_dep(r1);
+        const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * Cf::NKC * kTileDoms);
+
+        auto load = [&](int ch, uint32_t(&r)[32]) {
+          if constexpr (Cf::NKC == 1) {
+            ptx::tmem_ld32(tb + ch * 32, r);
+          } else {
+            ptx::tmem_ld16<0>(tb + ch * 16, r);
+            ptx::tmem_ld16<16>(tb + kTileDoms + ch * 16, r);
+          }
+        };
+
+        // fast screen of one chunk: the minimum float score over its
+        // columns and S (masked past the tile's last kept domain)
+        auto screen = [&](const float* c, int c0, int nvc, auto masked) {
+          constexpr bool MK = decltype(masked)::value;
+          float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
 #pragma unroll
-              for (int j = 0; j < 32; ++j) c[j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+          for (int j = 0; j < CW; j += 4) {
+            const float4 X = *(const float4*)(sX + c0 + j);
+            const float2 y01 = __ffma2_rn(nw2, make_float2(X.x, X.y), make_float2(c[j], c[j + 1]));
+            const float2 y23 = __ffma2_rn(nw2, make_float2(X.z, X.w), make_float2(c[j + 2], c[j + 3]));
+            if constexpr (MODE == MODE_GRID) {
+              const float4 U = *(const float4*)(sF0 + c0 + j);
+              const float4 G = *(const float4*)(sF1 + c0 + j);
+              const float yy[4] = {y01.x, y01.y, y23.x, y23.y};
+              const float uu[4] = {U.x, U.y, U.z, U.w};
+              const float gg[4] = {G.x, G.y, G.z, G.w};
+              float sc[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                float p = rintf(yy[u] * gg[u]);
+                p = fminf(fmaxf(p, 0.f), qf);
+                sc[u] = p * fmaf(p, uu[u], -yy[u]);
+                if constexpr (MK) sc[u] = j + u < nvc ? sc[u] : INFINITY;
+              }
+              m0 = ptx::fmin3(sc[0], sc[1], m0);
+              m1 = ptx::fmin3(sc[2], sc[3], m1);
             } else {
-              ptx::tmem_wait(r0);
-#pragma unroll
-              for (int j = 0; j < 32; ++j) c[j] = __uint_as_float(r0[j]);
+              const float4 F = *(const float4*)(sF0 + c0 + j);
+              float2 s01 = __ffma2_rn(np0, y01, make_float2(F.x, F.y));
+              float2 s23 = __ffma2_rn(np0, y23, make_float2(F.z, F.w));
+              if constexpr (MK) {
+                s01.x = j < nvc ? s01.x : INFINITY;
+                s01.y = j + 1 < nvc ? s01.y : INFINITY;
+                s23.x = j + 2 < nvc ? s23.x : INFINITY;
+                s23.y = j + 3 < nvc ? s23.y : INFINITY;
+              }
+              m0 = ptx::fmin3(s01.x, s01.y, m0);
+              m1 = ptx::fmin3(s23.x, s23.y, m1);
+              if constexpr (MODE == MODE_M2) {
+                const float4 F1 = *(const float4*)(sF1 + c0 + j);
+                float2 b01 = __ffma2_rn(np1, y01, make_float2(F1.x, F1.y));
+                float2 b23 = __ffma2_rn(np1, y23, make_float2(F1.z, F1.w));
+                if constexpr (MK) {
+                  b01.x = j < nvc ? b01.x : INFINITY;
+                  b01.y = j + 1 < nvc ? b01.y : INFINITY;
+                  b23.x = j + 2 < nvc ? b23.x : INFINITY;
+                  b23.y = j + 3 < nvc ? b23.y : INFINITY;
+                }
+                m2 = ptx::fmin3(b01.x, b01.y, m2);
+                m3 = ptx::fmin3(b23.x, b23.y, m3);
+              }
             }
-            // fast screen: the chunk's minimum float score (full chunks
-            // unmasked; the ragged last chunk masks columns >= nvc)
-            auto screen = [&](auto masked) {
-              // two columns per step, four independent running minima
-              float mn[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
-              auto score1 = [&](int j, float y, const float4& f) {
-                float s;
-                if constexpr (MODE == MODE_GRID) {
-                  float p = rintf(y * f.z);
-                  p = fminf(fmaxf(p, 0.f), qf);
-                  s = p * fmaf(p, f.y, -y);
-                } else {
-                  s = fmaf(-p0f, y, f.y);
-                }
-                if constexpr (decltype(masked)::value) s = j < nvc ? s : INFINITY;
-                return s;
-              };
+          }
+          return fminf(fminf(m0, m1), fminf(m2, m3));
+        };
+
+        // slow path: exact scores of every candidate of the chunk that can win.
+        // The lane marks its candidate columns (float score <= threshold) in
+        // bit masks, then scores only those exactly, reading their exact
+        // correlations back from its own column of the scratch.
+        auto slow = [&](const float* c, int c0, int nvc, float mn) {
+          if (mn <= thr) {
+            // the chunk's best float candidate is scored exactly below, so
+            // nothing more than 2 delta above it can win either
+            const float cut = fminf(thr, __fadd_ru(mn, 2.f * delta));
+            uint32_t mk0 = 0, mk1 = 0;
 #pragma unroll
-              for (int j = 0; j < 32; j += 2) {
-                const float4 fa = Df[cc * 32 + j], fb = Df[cc * 32 + j + 1];
-                const float ya = fmaf(-w, fa.x, c[j]), yb = fmaf(-w, fb.x, c[j + 1]);
-                float& m = mn[(j >> 1) & 3];
+            for (int j = 0; j < CW; j += 2) {
+              const float2 X2 = *(const float2*)(sX + c0 + j);
+              const float2 y = __ffma2_rn(nw2, X2, make_float2(c[j], c[j + 1]));
+              if constexpr (MODE == MODE_GRID) {
+                const float2 U = *(const float2*)(sF0 + c0 + j);
+                const float2 G = *(const float2*)(sF1 + c0 + j);
+                float pa = fminf(fmaxf(rintf(y.x * G.x), 0.f), qf);
+                float pb = fminf(fmaxf(rintf(y.y * G.y), 0.f), qf);
+                if (pa * fmaf(pa, U.x, -y.x) <= cut) mk0 |= 1u << j;
+                if (pb * fmaf(pb, U.y, -y.y) <= cut) mk0 |= 2u << j;
+              } else {
+                const float2 F = *(const float2*)(sF0 + c0 + j);
+                const float2 s0 = __ffma2_rn(np0, y, F);
+                if (s0.x <= cut) mk0 |= 1u << j;
+                if (s0.y <= cut) mk0 |= 2u << j;
                 if constexpr (MODE == MODE_M2) {
-                  float a0 = fmaf(-p0f, ya, fa.y), a1 = fmaf(-p1f, ya, fa.z);
-                  float b0 = fmaf(-p0f, yb, fb.y), b1 = fmaf(-p1f, yb, fb.z);
-                  if constexpr (decltype(masked)::value) {
-                    a0 = j < nvc ? a0 : INFINITY;
-                    a1 = j < nvc ? a1 : INFINITY;
-                    b0 = j + 1 < nvc ? b0 : INFINITY;
-                    b1 = j + 1 < nvc ? b1 : INFINITY;
-                  }
-                  m = ptx::fmin3(ptx::fmin3(a0, a1, b0), b1, m);
-                } else {
-                  m = ptx::fmin3(score1(j, ya, fa), score1(j + 1, yb, fb), m);
+                  const float2 F1 = *(const float2*)(sF1 + c0 + j);
+                  const float2 s1 = __ffma2_rn(np1, y, F1);
+                  if (s1.x <= cut) mk1 |= 1u << j;
+                  if (s1.y <= cut) mk1 |= 2u << j;
                 }
               }
-              return fminf(fminf(mn[0], mn[1]), fminf(mn[2], mn[3]));
-            };
-            const float mn = nvc >= 32 ? screen(std::false_type{}) : screen(std::true_type{});
-            if (__any_sync(0xffffffffu, mn <= best.thr)) {
-              // slow path: exact scores of every candidate that can win
+            }
+            const uint32_t lim = nvc >= 32 ? 0xffffffffu : (1u << nvc) - 1u;
+            mk0 &= lim;
+            mk1 &= lim;
+            if (mk0 | mk1) {
 #pragma unroll
-              for (int j = 0; j < 32; ++j) scr[j * 32 + lane] = c[j];
-              __syncwarp();
-              if (mn <= best.thr) {
-                const int jn = nvc < 32 ? nvc : 32;
-#pragma unroll 1
-                for (int j = 0; j < jn; ++j) {
-                  const float cf = scr[j * 32 + lane];
-                  const float4 f = Df[cc * 32 + j];
-                  const float y = fmaf(-w, f.x, cf);
-                  if constexpr (MODE == MODE_GRID) {
-                    float p = rintf(y * f.z);
-                    p = fminf(fmaxf(p, 0.f), qf);
-                    const float s = p * fmaf(p, f.y, -y);
-                    if (s <= best.thr) {
-                      const int pi = (int)p;
-                      for (int pp = max(pi - 1, 0); pp <= min(pi + 1, qv); ++pp)
-                        exact(t, cc * 32 + j, cf, pp);
-                    }
-                  } else {
-                    if (fmaf(-p0f, y, f.y) <= best.thr) exact(t, cc * 32 + j, cf, 0);
-                    if constexpr (MODE == MODE_M2)
-                      if (fmaf(-p1f, y, f.z) <= best.thr) exact(t, cc * 32 + j, cf, 1);
-                  }
+              for (int j = 0; j < CW; ++j) scr[j * 32 + lane] = c[j];
+              while (mk0) {
+                const int j = __ffs(mk0) - 1;
+                mk0 &= mk0 - 1;
+                const int col = c0 + j;
+                const float cf = scr[j * 32 + lane];
+                if constexpr (MODE == MODE_GRID) {
+                  const float y = fmaf(-w, sX[col], cf);
+                  const int pi = (int)fminf(fmaxf(rintf(y * sF1[col]), 0.f), qf);
+                  for (int pp = max(pi - 1, 0); pp <= min(pi + 1, qv); ++pp)
+                    exact(sDom, col, cf, pp);
+                } else {
+                  exact(sDom, col, cf, 0);
                 }
               }
-              __syncwarp();
+              while (mk1) {
+                const int j = __ffs(mk1) - 1;
+                mk1 &= mk1 - 1;
+                exact(sDom, c0 + j, scr[j * 32 + lane], 1);
+              }
+            }
+          }
+          __syncwarp();
+          // the 8 isometry rows of a range share the tightest threshold
+          float t8 = thr;
+          t8 = fminf(t8, __shfl_xor_sync(0xffffffffu, t8, 1));
+          t8 = fminf(t8, __shfl_xor_sync(0xffffffffu, t8, 2));
+          t8 = fminf(t8, __shfl_xor_sync(0xffffffffu, t8, 4));
+          if (valid) {
+            thr = t8;
+            if (improved) {
+              atomicMin(gth, thr_to_ord(thr));
+              improved = false;
+            }
+          }
+        };
+
+        auto chunk = [&](int ch, const uint32_t* r) {
+          const int c0 = ch * CW;
+          float c[CW];
+          if constexpr (Cf::NKC == 1) {
+#pragma unroll
+            for (int j = 0; j < CW; ++j) c[j] = __uint_as_float(r[j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < CW; j += 2) {
+              const float2 s2 =
+                  __fadd2_rn(make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])),
+                             make_float2(__uint_as_float(r[16 + j]), __uint_as_float(r[17 + j])));
+              c[j] = s2.x;
+              c[j + 1] = s2.y;
+            }
+          }
+          const int nvc = nv - c0;
+          const float mn = nvc >= CW ? screen(c, c0, nvc, std::false_type{})
+                                     : screen(c, c0, nvc, std::true_type{});
+          if (__any_sync(0xffffffffu, mn <= thr)) slow(c, c0, nvc, mn);
+        };
+
+        if (ok) {
+          if constexpr (EG == 2) {
+            // two warps per sub-partition: overlap the next chunk's TMEM
+            // load with this chunk's scoring
+            uint32_t ra[32], rb[32];
+            load(0, ra);
+#pragma unroll
+            for (int ch = 0; ch < Cf::NCH; ch += 2) {
+              if (ch * CW >= nv) break;
+              ptx::tmem_wait(ra);
+              if ((ch + 1) * CW < nv) load(ch + 1, rb);
+              chunk(ch, ra);
+              if ((ch + 1) * CW >= nv) break;
+              ptx::tmem_wait(rb);
+              if (ch + 2 < Cf::NCH && (ch + 2) * CW < nv) load(ch + 2, ra);
+              chunk(ch + 1, rb);
+            }
+          } else {
+            // three warps per sub-partition hide the load latency
+#pragma unroll 1
+            for (int ch = 0; ch < Cf::NCH; ++ch) {
+              if (ch * CW >= nv) break;
+              uint32_t ra[32];
+              load(ch, ra);
+              ptx::tmem_wait(ra);
+              chunk(ch, ra);
             }
           }
         }
         ptx::tc_fence_before();
         __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
-        ++ti;
+        if (lane == 0) {
+          ptx::mbar_arrive(&acc_empty[ab]);
+          ptx::mbar_arrive(&d_empty[db]);
+        }
       }
-      Cand out;
-      out.score = valid ? best.e : INT64_MAX;
-      out.key = valid ? best.key : INT64_MAX;
-      a.part[it * kTileRows + row] = out;
+      // merge the groups' bests of this row; group 0 writes the partial
+      if (h > 0) mrg[(h - 1) * kTileRows + row] = Cand{best_e, best_key};
+      ptx::named_bar_sync(1 + qd, 32 * EG);
+      if (h == 0) {
+#pragma unroll
+        for (int o2 = 0; o2 < EG - 1; ++o2) {
+          const Cand o = mrg[o2 * kTileRows + row];
+          if (o.score < best_e || (o.score == best_e && o.key < best_key)) {
+            best_e = o.score;
+            best_key = o.key;
+          }
+        }
+        Cand out;
+        out.score = valid ? best_e : INT64_MAX;
+        out.key = valid ? best_key : INT64_MAX;
+        a.part[it * kTileRows + row] = out;
+      }
+      ptx::named_bar_sync(1 + qd, 32 * EG);
     }
   }
 
@@ -414,16 +626,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(MatchArgs a) {
 // ---------------------------------------------------------------- host side
 template <int B, int MODE>
 static int launch_tc_BM(const MatchArgs& a, int grid, cudaStream_t st) {
-  k_match_tc<B, MODE><<<grid, kTcThreads, TcCfg<B>::SMEM + 1024, st>>>(a);
+  k_match_tc<B, MODE><<<grid, TcCfg<B>::Wp::THREADS, TcCfg<B>::SMEM + 128, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
 }
 
 template <int B, int MODE>
 static int prepare_BM() {
-  return cudaFuncSetAttribute(k_match_tc<B, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              TcCfg<B>::SMEM + 1024) == cudaSuccess
-             ? 0
-             : 1;
+  if (cudaFuncSetAttribute(k_match_tc<B, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           TcCfg<B>::SMEM + 128) != cudaSuccess)
+    return 1;
+  // the warpgroups' register split is paid for by the launch allocation
+  cudaFuncAttributes at{};
+  if (cudaFuncGetAttributes(&at, k_match_tc<B, MODE>) != cudaSuccess) return 1;
+  return at.numRegs >= TcCfg<B>::Wp::LREGS ? 0 : 1;
 }
 
 template <int B>

@@ -273,12 +273,15 @@ k_pack_domains(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
                const SelState* __restrict__ st, const int32_t* __restrict__ kept,
                const int32_t* __restrict__ sd, const int32_t* __restrict__ sq, SSet S,
                uint16_t* __restrict__ bpack, float* __restrict__ b32, DomRec* __restrict__ dom,
-               float4* __restrict__ domf) {
+               float* __restrict__ domf, unsigned int* __restrict__ umax) {
   using Gm = PoolGeom<B>;
   constexpr int G = Gm::G;
   constexpr int n = B * B;
   constexpr int Kp = PackGeom<B>::Kp;
   const int grp = threadIdx.x / G, gl = threadIdx.x % G;
+  __shared__ unsigned int s_umax;
+  if (threadIdx.x == 0) s_umax = 0;
+  __syncthreads();
   const int64_t S_tot = slot_off[n_images];
   for (int64_t slot = (int64_t)blockIdx.x * Gm::GPB + grp; slot < S_tot;
        slot += (int64_t)gridDim.x * Gm::GPB) {
@@ -308,22 +311,30 @@ k_pack_domains(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
       // Scores are E' / (8 q n) with E' = p^2 V - 8 p q C (see the match
       // kernels): explicit sets store p_t^2 V / (8 q n); the grid stores
       // V / (8 q n) and 4 q n / V, the scale of the real minimiser
-      // p* = 4 q C / V.
+      // p* = 4 q C / V.  Layout: per 128-slot tile, four planes of 128
+      // floats {sum Ds', F0, F1, 0}, so a tile's constants are one
+      // contiguous 2 KB block and each plane loads as float4 vectors.
       const double u = (double)r.v / (8.0 * S.q * n);
-      float4 f;
-      f.x = (float)r.sdp;
+      // largest u of the level (non-negative floats order as their bits):
+      // bounds the scores' rounding errors in the matcher
+      atomicMax(&s_umax, __float_as_uint(__double2float_ru(u)));
+      float f0, f1;
       if (S.grid) {
-        f.y = (float)u;
-        f.z = r.v > 0 ? (float)(4.0 * S.q * n / (double)r.v) : 0.0f;
-        f.w = 0.0f;
+        f0 = (float)u;
+        f1 = r.v > 0 ? (float)(4.0 * S.q * n / (double)r.v) : 0.0f;
       } else {
-        f.y = (float)(u * S.p[0] * S.p[0]);
-        f.z = S.m > 1 ? (float)(u * S.p[1] * S.p[1]) : 0.0f;
-        f.w = 0.0f;
+        f0 = (float)(u * S.p[0] * S.p[0]);
+        f1 = S.m > 1 ? (float)(u * S.p[1] * S.p[1]) : 0.0f;
       }
-      domf[slot] = f;
+      float* ft = domf + (slot >> 7) * (4 * kTileDoms) + (slot & 127);
+      ft[0] = (float)r.sdp;
+      ft[kTileDoms] = f0;
+      ft[2 * kTileDoms] = f1;
+      ft[3 * kTileDoms] = 0.0f;
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_umax) atomicMax(umax, s_umax);
 }
 
 // ---------------------------------------------------------------- driver
@@ -370,6 +381,7 @@ int pool_build(PoolLevel& pl, const int64_t* d_dT, cudaStream_t st) {
   FIC_CUDA_TRY(scan_compact(kc, P, pl.scan_scratch.as<int32_t>(), pl.total.as<int64_t>(), st));
 
   const int nsm = pl.nsm > 0 ? pl.nsm : 148;
+  FIC_CUDA_TRY(cudaMemsetAsync(pl.umax.p, 0, sizeof(unsigned int), st));
   uint16_t* bp = pl.want_tc ? pl.bpack.as<uint16_t>() : nullptr;
   float* b32 = pl.want_f32 ? pl.b32.as<float>() : nullptr;
 #define FIC_PACK(BB)                                                                           \
@@ -381,7 +393,7 @@ int pool_build(PoolLevel& pl, const int64_t* d_dT, cudaStream_t st) {
         pl.img.as<ImgDev>(), off, pl.slot_off.as<int64_t>(), ni, pl.L, sel,                    \
         pl.kept.as<int32_t>(),                                                                 \
         pl.sd.as<int32_t>(), pl.sq.as<int32_t>(), pl.sset, bp, b32, pl.dom.as<DomRec>(),       \
-        pl.domf.as<float4>());                                                                 \
+        pl.domf.as<float>(), pl.umax.as<unsigned int>());                                     \
   }
   switch (pl.B) {
     case 16: FIC_PACK(16) break;

@@ -89,6 +89,13 @@ MATCH_CASES = [
     (96, 64, 14, 16, 1, 1, 16, 20),
     (48, 48, 15, 2, 2, 1, 10, 120),
     (64, 64, 16, 4, 1, 1, 16, 90),
+    # many domain tiles per work item and many items per range tile: the
+    # thresholds shared between isometry rows, warp pairs and CTAs
+    (256, 256, 31, 4, 1, 0, 16, 300),
+    (256, 192, 32, 8, 1, 1, 16, 60),
+    (256, 256, 33, 16, 2, 0, 16, None),
+    (320, 160, 34, 2, 1, 0, 16, 500),
+    (256, 256, 35, 16, 1, 1, 32, 12),
 ]
 
 
