@@ -354,7 +354,7 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
   return launch_reduce_final(w.B, pl.img.as<ImgDev>(), w.rec.as<RangeRec>(), w.n_act.as<int64_t>(),
                              w.cap, w.act_off.as<int64_t>(), pl.slot_off.as<int64_t>(), ni, pl.L,
                              pl.sel.as<SelState>(), w.item_off.as<int64_t>(),
-                             w.chunks.as<int32_t>(), w.part.as<Cand>(), pl.sset, level,
+                             w.chunks.as<int32_t>(), w.part.as<Cand>(), tc ? 1 : 8, pl.sset, level,
                              w.meta.as<PlanMeta>(), ctx->status.as<uint32_t>(),
                              w.res.as<fic_transform>(), st);
 }

@@ -149,8 +149,9 @@ __global__ void k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* 
                                const SelState* __restrict__ sel,
                                const int64_t* __restrict__ item_off,
                                const int32_t* __restrict__ chunks, const Cand* __restrict__ part,
-                               SSet S, int level, const PlanMeta* __restrict__ meta,
-                               uint32_t* __restrict__ status, fic_transform* __restrict__ res) {
+                               int iso_rows, SSet S, int level,
+                               const PlanMeta* __restrict__ meta, uint32_t* __restrict__ status,
+                               fic_transform* __restrict__ res) {
   constexpr int n = B * B;
   const int64_t N = *n_act;
   const bool overflow = meta->overflow != 0;
@@ -165,8 +166,8 @@ __global__ void k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* 
     const int nc = overflow ? 0 : chunks[im];
     Cand best{INT64_MAX, INT64_MAX};
     for (int c = 0; c < nc; ++c) {
-      const Cand* p = part + (item_off[im] + m * nc + c) * kTileRows + rr * 8;
-      for (int k = 0; k < 8; ++k) {
+      const Cand* p = part + ((item_off[im] + m * nc + c) * kTileRanges + rr) * iso_rows;
+      for (int k = 0; k < iso_rows; ++k) {
         const Cand x = p[k];
         if (x.score < best.score || (x.score == best.score && x.key < best.key)) best = x;
       }
@@ -230,15 +231,16 @@ __global__ void k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* 
 int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
                         int64_t cap, const int64_t* act_off, const int64_t* pool_off,
                         int n_images, int L, const SelState* sel, const int64_t* item_off,
-                        const int32_t* chunks, const Cand* part, const SSet& S, int level,
-                        const PlanMeta* meta, uint32_t* status, fic_transform* res,
+                        const int32_t* chunks, const Cand* part, int iso_rows, const SSet& S,
+                        int level, const PlanMeta* meta, uint32_t* status, fic_transform* res,
                         cudaStream_t st) {
   const int threads = 128;
   int grid = (int)ceil_div64(cap > 0 ? cap : 1, threads);
   if (grid > 65535) grid = 65535;
 #define FIC_RF(BB)                                                                           \
   k_reduce_final<BB><<<grid, threads, 0, st>>>(imgs, rec, n_act, act_off, pool_off, n_images, \
-                                               L, sel, item_off, chunks, part, S, level, meta, \
+                                               L, sel, item_off, chunks, part, iso_rows, S,  \
+                                               level, meta,                                   \
                                                status, res)
   switch (B) {
     case 16: FIC_RF(16); break;

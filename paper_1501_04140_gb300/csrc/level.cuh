@@ -34,7 +34,8 @@ struct MatchArgs {
   const int64_t* item_off;          // n_images + 1
   const int32_t* chunks;            // per image
   const PlanMeta* meta;
-  Cand* part;                       // items x 128
+  Cand* part;                       // per item: 16 ranges x 8 isometry rows (FP32 path)
+                                    // or 16 ranges (tensor path)
   uint32_t* status;                 // device status word
 };
 
@@ -60,8 +61,8 @@ __global__ void k_plan(int n_images, const int64_t* act_off, const int64_t* act_
 int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
                         int64_t cap, const int64_t* act_off, const int64_t* pool_off,
                         int n_images, int L, const SelState* sel, const int64_t* item_off,
-                        const int32_t* chunks, const Cand* part, const SSet& S, int level,
-                        const PlanMeta* meta, uint32_t* status, fic_transform* res,
+                        const int32_t* chunks, const Cand* part, int iso_rows, const SSet& S,
+                        int level, const PlanMeta* meta, uint32_t* status, fic_transform* res,
                         cudaStream_t st);
 
 int launch_split(const fic_transform* res, const RangeRec* rec, const int64_t* n_act, int64_t cap,

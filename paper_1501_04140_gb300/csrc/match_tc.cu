@@ -3,49 +3,59 @@
 // Sec. 2's search scores every range against every kept domain under the 8
 // isometries.  With the isometries applied to the range (<R, T_k D> =
 // <T_k^-1 R, D>), the correlations of a level form one dense contraction
-//     corr[(range, k), domain] = sum_i (T_k^-1 R)_i (Ds_i - 512) ,  K = n,
-// with rows r - 128 in [-128, 127] and columns Ds - 512 in [-512, 508]: small
+//     corr[domain, (range, k)] = sum_i (Ds_i - 512) (T_k^-1 R)_i ,  K = n,
+// with columns r - 128 in [-128, 127] and rows Ds - 512 in [-512, 508]: small
 // integers, exact in binary16.  Each 128-wide K slice keeps every partial sum
 // below 2^23 in magnitude (128 * 512 * 128), so the f32 accumulators of
 // tcgen05.mma kind::f16 hold the exact integer correlation; B = 16 (K = 256)
 // uses two accumulators, one per K half, added as exact integers.
 //
+// Orientation.  The streamed 128-domain tile is the MMA's A operand (M =
+// 128: one TMEM lane per domain) and the resident tile of 16 ranges x 8
+// isometries is its B operand (N = 128 columns, the 8 isometries of a range
+// adjacent).  An epilogue thread owns one domain: its per-domain constants
+// sit in registers, and a range's 8 isometries are 8 of its own columns.
+//
+// Isometry reduction.  For s = p/q, E of Eq. 1 with o from Eq. 3 is, up to
+// the range-only term, E' = p^2 V - 8 p q C with C = n <r', Ds'> - sum r'
+// sum Ds' (exact integers).  V and both sums are the same for the 8
+// isometric copies, so for p > 0 E' falls strictly as the correlation
+// rises: of a (domain, range) pair, the isometry with the largest
+// correlation (the lowest k among equals) wins for every s > 0, and for
+// p = 0 every isometry gives E' = 0, where k = 0 has the lowest tie-break
+// key.  The epilogue therefore reduces the 8 exact correlations to their
+// maximum before any scoring: one score per (domain, range) and s.
+//
 // Warp roles of one persistent CTA per SM:
-//   warp 0      producer: bulk copies (TMA engine) of the resident 128-row
-//               range tile, the streamed 128-domain tiles (one stage per K
-//               half at B = 16) and each tile's per-domain scoring planes
-//               and exact records;
+//   warp 0      producer: bulk copies (TMA engine) of the resident range
+//               tile, the streamed 128-domain tiles (one stage per K half at
+//               B = 16) and each tile's per-domain scoring planes and exact
+//               records;
 //   warp 1      allocates tensor memory and issues the MMAs (one thread);
 //   warps 2-3   idle (they complete the control warpgroup);
-//   warps 4-    epilogue, EG groups of four warps (EG = 3, or 2 at B = 16
-//               where shared memory is short): each warp owns the 32 TMEM
-//               lanes = 32 rows (range, isometry) of its quarter; the groups
-//               take turns on the tiles and merge their row bests per item.
+//   warps 4-    epilogue, EG groups of four warps: each warp owns the 32 TMEM
+//               lanes = 32 domains of its quarter; the groups take turns on
+//               the tiles and merge their per-range bests per item.
 //
-// Epilogue.  For s = p/q, E of Eq. 1 with o from Eq. 3 is, up to the
-// range-only term, E' = p^2 V - 8 p q C with C = n <r', Ds'> - sum r' sum Ds'
-// (exact integers).  The float score E' / (8 q n) = p^2 u - p y, with
-// u = V / (8 q n) and y = C / n = corr - (sum r' / n) sum Ds', screens the
-// candidates: a column is skipped only when its float score exceeds the
-// row's best exact score by more than the level's rounding bound `delta`;
-// every other candidate is scored exactly in int64 and compared with the
-// tie-break key (pos * 8 + k) * |S| + s_idx.  The result therefore equals the
-// exhaustive exact argmin.  A threshold only has to bound the exact score of
-// some candidate of the same range that stays in the reduction, so the 8
-// isometry rows of a range share theirs (warp shuffles) and every CTA that
-// scores the range shares it through a per-range word in global memory
-// (atomicMin on an order-preserving image of the float).  Scores of two
-// columns at a time use the packed f32x2 FMA.
+// Screening.  The float score E' / (8 q n) = p^2 u - p y, with
+// u = V / (8 q n) and y = C / n = cmax - (sum r' / n) sum Ds', screens the
+// pairs: a pair is skipped only when its best float score exceeds the
+// range's threshold -- the exact score of a candidate already kept plus the
+// rounding bound `delta`; every other pair is scored exactly in int64 and
+// compared with the tie-break key (pos * 8 + k) * |S| + s_idx.  The result
+// therefore equals the exhaustive exact argmin.  A threshold only has to
+// bound the exact score of some candidate of the same range that stays in
+// the reduction, so the warp's 32 domains share theirs (warp shuffles) and
+// every CTA that scores the range shares it through a per-range word in
+// global memory (atomicMin on an order-preserving image of the float).
 //
-// Rounding bound.  corr is exact, w = sum r' / n is exact (n is a power of
+// Rounding bound.  cmax is exact, w = sum r' / n is exact (n is a power of
 // two) and the FMAs round once each, so y carries at most 2^-24 |y| and a
 // score F - p y (F = p^2 u rounded from double) at most
 //     2^-23 (F + p |y|) <= 2^-23 (p^2 umax + p Y),   Y = 1024 sum |r'|,
 // because |corr| <= 512 sum |r'| and |w sum Ds'| <= 512 |sum r'|; umax is the
 // largest u of the level's kept domains.  The kernel uses 4x that bound
-// (`delta`), per range.  A chunk's best float candidate X is scored exactly,
-// so any candidate whose float score exceeds X's by more than 2 delta is
-// strictly worse than X and is skipped as well.
+// (`delta`), per range.
 //
 // Grid S (s = p / q, p = 0..q).  E'(p) = V (p - p*)^2 + const with the real
 // minimiser p* = 4 q C / V, so the best grid point is the nearest integer to
@@ -97,12 +107,13 @@ struct TcCfg {
   static constexpr int ND = B == 16 ? 4 : B == 8 ? 8 : 16;    // scoring-record stages
   static constexpr int TCOLS = 512;
   static constexpr int CW = NKC == 1 ? 32 : 16;       // tile columns per epilogue chunk
-  static constexpr int NCH = kTileDoms / CW;
+  static constexpr int RPC = CW / 8;                  // ranges per chunk
+  static constexpr int NCH = kTileRows / CW;
   static constexpr int DT_BYTES = 4 * kTileDoms * 4;  // float planes {sum Ds', F0, F1, 0}
-  static constexpr int DR_BYTES = kTileDoms * 16;     // DomRec per column
+  static constexpr int DR_BYTES = kTileDoms * 16;     // DomRec per domain
   static constexpr int D_BYTES = DT_BYTES + DR_BYTES;
-  static constexpr int MRG_BYTES = (EG - 1) * kTileRows * 16;
-  static constexpr int SCR_BYTES = Wp::EPI_WARPS * 32 * CW * 4;
+  static constexpr int MRG_BYTES = Wp::EPI_WARPS * kTileRanges * 16;  // per-warp range bests
+  static constexpr int SCR_BYTES = 3 * kTileRanges * 4;  // per range: w, delta, threshold
   static constexpr int OFF_B = A_BYTES;
   static constexpr int OFF_D = OFF_B + NST * ST_BYTES;
   static constexpr int OFF_MRG = OFF_D + ND * D_BYTES;
@@ -141,9 +152,12 @@ __device__ inline ItemGeo item_geo(const MatchArgs& a, int64_t it, int CH) {
   return g;
 }
 
-// Skip a candidate whose float score is above this (exact E' plus the margin).
-__device__ inline float thr_of(int64_t e, double inv8qn, float delta) {
-  return __double2float_ru(fma((double)e, inv8qn, (double)delta));
+// Skip a candidate whose float score is above this: an upper bound of the
+// exact score E' / (8 q n) plus the margin, in directed-rounding FP32
+// (inv_up / inv_dn: 1 / (8 q n) rounded up / down).
+__device__ inline float thr_of(int64_t e, float inv_up, float inv_dn, float delta) {
+  const float ef = __ll2float_ru(e);
+  return __fadd_ru(__fmul_ru(ef, ef >= 0.f ? inv_up : inv_dn), delta);
 }
 
 template <int B, int MODE>
@@ -265,7 +279,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t IDESC = ptx::idesc_f16_f32(kTileRows, kTileDoms);
+      constexpr uint32_t IDESC = ptx::idesc_f16_f32(kTileDoms, kTileRows);
       uint32_t bi = 0, ai = 0, ti = 0;
       bool ok = true;
       for (int64_t it = blockIdx.x; ok && it < items; it += gridDim.x) {
@@ -291,9 +305,11 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
 #pragma unroll
             for (int s = 0; s < Cf::KSTEPS; ++s) {
               const int kk = (kc * Cf::KSTEPS + s) * 2;  // core-matrix column of A
-              const uint64_t ad = ptx::smem_desc(sA + kk * 128, 128, 16 * Cf::Kp);
-              const uint64_t bd = ptx::smem_desc(sB + st * Cf::ST_BYTES + s * 256, 128, 16 * Cf::KS);
-              ptx::mma_f16(d, ad, bd, IDESC, s > 0 ? 1u : 0u);
+              // A = the domain stage (one TMEM lane per domain), B = the
+              // resident range tile (columns = range x isometry)
+              const uint64_t rd = ptx::smem_desc(sA + kk * 128, 128, 16 * Cf::Kp);
+              const uint64_t dd = ptx::smem_desc(sB + st * Cf::ST_BYTES + s * 256, 128, 16 * Cf::KS);
+              ptx::mma_f16(d, dd, rd, IDESC, s > 0 ? 1u : 0u);
             }
             ptx::mma_commit(&empty_b[st]);
             ++bi;
@@ -312,67 +328,74 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
   } else {
     ptx::setmaxnreg_inc<Cf::Wp::EREGS>();
     // ------------------------------------------------------------ epilogue
-    // Warps 4..: quarter qd = warp % 4 of the TMEM lanes (rows); group h
-    // takes the tiles ti = h mod EG.  The groups' row bests merge at item end.
+    // Warps 4..: quarter qd = warp % 4 of the TMEM lanes = the tile's domains
+    // qd * 32 .. qd * 32 + 31; group h takes the tiles ti = h mod EG.  Each
+    // warp keeps its best candidate per range of the item in shared memory;
+    // the warps' bests merge at item end.  Per item the first epilogue warp
+    // stages each range's w, rounding bound and starting threshold (the best
+    // any CTA has published) in shared memory; the warps share their
+    // threshold improvements there (a plain store of a smaller value: a lost
+    // race only leaves a looser, still valid, threshold) and publish them to
+    // the other CTAs with atomicMin.
+    constexpr int RPC = Cf::RPC;
+    constexpr int REFRESH = 4;               // tiles between reads of the global thresholds
     const int ew = warp - kCtlWarps;
     const int h = ew >> 2;
     const int qd = warp & 3;
-    const int row = qd * 32 + lane;          // tile row = (range, isometry)
-    const int k_iso = row & 7;
-    float* scr = (float*)(smem + Cf::OFF_SCR) + ew * 32 * CW;
-    Cand* mrg = (Cand*)(smem + Cf::OFF_MRG);
+    const int dl = qd * 32 + lane;           // tile row = domain slot in the tile
+    const uint32_t epi_threads = 32 * Cf::Wp::EPI_WARPS;
+    Cand* wbest = (Cand*)(smem + Cf::OFF_MRG);  // [EPI_WARPS][16]
+    Cand* mybest = wbest + ew * kTileRanges;
+    float* sW = (float*)(smem + Cf::OFF_SCR);
+    float* sDelta = sW + kTileRanges;
+    float* sThr = sW + 2 * kTileRanges;
     const int m_s = a.S.m;
     const int qv = a.S.q;
-    const double inv8qn = 1.0 / (8.0 * qv * n);
-    const double umax = (double)*a.umax;
-    const double pmx = (double)(MODE == MODE_M2 ? max(a.S.p[0], a.S.p[1]) : a.S.p[0]);
+    const float inv_up = __double2float_ru(1.0 / (8.0 * qv * n));
+    const float inv_dn = __double2float_rd(1.0 / (8.0 * qv * n));
     const float p0f = (float)a.S.p[0], p1f = (float)a.S.p[1];
     const float qf = (float)qv;
-    const float2 np0 = make_float2(-p0f, -p0f), np1 = make_float2(-p1f, -p1f);
+    const int rl = lane & (kTileRanges - 1);
     uint32_t ti = 0;
     bool ok = true;
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
       const ItemGeo g = item_geo(a, it, CH);
-      const int rr = row >> 3;
-      const bool valid = rr < g.nr;
-      int32_t srp = 0, sabs = 0;
-      if (valid) {
-        const RangeMom m = a.mom[g.r0 + rr];
-        srp = m.srp;
-        sabs = m.sabs;
-      }
-      // rounding bound of this range's float scores (score units), the same
-      // for its 8 rows in every CTA: 4x the bound derived above
-      const float delta =
-          MODE == MODE_GRID
-              ? a.delta
-              : __double2float_ru(ldexp(pmx * pmx * umax + pmx * 1024.0 * (double)sabs, -21));
-      const float w = (float)srp / (float)n;
-      const float2 nw2 = make_float2(-w, -w);
-      uint32_t* gth = a.gthr + (g.r0 + (valid ? rr : 0));
-      uint32_t gpre = valid ? __ldcg(gth) : kThrInit;
-      int64_t best_e = INT64_MAX, best_key = INT64_MAX;
-      float thr = valid ? INFINITY : -INFINITY;
-      bool improved = false;
-
-      // exact score of one candidate (tile column col, set index si)
-      auto exact = [&](const DomRec* sDom, int col, float cf, int si) {
-        const DomRec d = sDom[col];
-        const int64_t ci = (int64_t)(int)cf;
-        const int64_t C = (ci << LOGN) - (int64_t)srp * (int64_t)d.sdp;
-        const int64_t p = (MODE == MODE_GRID) ? si : a.S.p[si];
-        const int64_t e = p * p * d.v - 8 * p * qv * C;
-        const int64_t key = ((int64_t)d.pos * 8 + k_iso) * m_s + si;
-        if (e < best_e || (e == best_e && key < best_key)) {
-          best_e = e;
-          best_key = key;
-          const float to = thr_of(e, inv8qn, delta);
-          if (to < thr) {
-            thr = to;
-            improved = true;
+      const bool rv = rl < g.nr;
+      if (ew == 0 && lane < kTileRanges) {
+        float wv = 0.f, dv = 0.f, tv = -INFINITY;
+        if (rv) {
+          const RangeMom m = a.mom[g.r0 + rl];
+          wv = (float)m.srp * (1.0f / n);
+          // rounding bound of this range's float scores (score units): 4x
+          // the bound derived above; the grid uses the level-wide margin
+          if (MODE == MODE_GRID) {
+            dv = a.delta;
+          } else {
+            const double pmx = (double)(MODE == MODE_M2 ? max(a.S.p[0], a.S.p[1]) : a.S.p[0]);
+            dv = __double2float_ru(
+                ldexp(pmx * pmx * (double)*a.umax + pmx * 1024.0 * (double)m.sabs, -21));
           }
+          tv = ord_to_thr(__ldcg(a.gthr + g.r0 + rl));
         }
-      };
+        sW[lane] = wv;
+        sDelta[lane] = dv;
+        sThr[lane] = tv;
+      }
+      // (the first epilogue warp has merged the previous item's bests and
+      // staged this item's ranges when every warp passes this barrier)
+      ptx::named_bar_sync(1, epi_threads);
+      if (lane < kTileRanges) mybest[lane] = Cand{INT64_MAX, INT64_MAX};
+      __syncwarp();
+      float w[kTileRanges], thr[kTileRanges];
+#pragma unroll
+      for (int r = 0; r < kTileRanges; r += 4) {
+        const float4 wv = *(const float4*)(sW + r);
+        const float4 tv = *(const float4*)(sThr + r);
+        w[r] = wv.x, w[r + 1] = wv.y, w[r + 2] = wv.z, w[r + 3] = wv.w;
+        thr[r] = tv.x, thr[r + 1] = tv.y, thr[r + 2] = tv.z, thr[r + 3] = tv.w;
+      }
+      uint32_t gpre = rv ? __ldcg(a.gthr + g.r0 + rl) : kThrInit;
+      int nmine = 0;
 
       for (int t = g.t0; t < g.t1; ++t, ++ti) {
         if ((int)(ti % EG) != h) continue;
@@ -385,206 +408,159 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
         if (ok && !all && lane == 0) fail();
         ok = all;
         ptx::tc_fence_after();
-        // threshold found by any CTA for this range (loaded one tile ahead)
-        if (valid) thr = fminf(thr, ord_to_thr(gpre));
-        gpre = valid ? __ldcg(gth) : kThrInit;
-        const float* sX = (const float*)(smem + Cf::OFF_D + db * Cf::D_BYTES);
-        const float* sF0 = sX + kTileDoms;
-        const float* sF1 = sX + 2 * kTileDoms;
-        const DomRec* sDom = (const DomRec*)(smem + Cf::OFF_D + db * Cf::D_BYTES + Cf::DT_BYTES);
+        // thresholds of the other warps (shared memory, every tile) and of
+        // the other CTAs (global, loaded REFRESH tiles ahead, passed on
+        // through shared memory)
+        if (++nmine % REFRESH == 0) {
+          if (lane < kTileRanges && rv) {
+            const float tg = ord_to_thr(gpre);
+            if (tg < sThr[lane]) sThr[lane] = tg;
+          }
+          gpre = rv ? __ldcg(a.gthr + g.r0 + rl) : kThrInit;
+        }
+#pragma unroll
+        for (int r = 0; r < kTileRanges; r += 4) {
+          const float4 tv = *(const float4*)(sThr + r);
+          thr[r] = fminf(thr[r], tv.x);
+          thr[r + 1] = fminf(thr[r + 1], tv.y);
+          thr[r + 2] = fminf(thr[r + 2], tv.z);
+          thr[r + 3] = fminf(thr[r + 3], tv.w);
+        }
+        const uint8_t* sD = smem + Cf::OFF_D + db * Cf::D_BYTES;
+        const float* sX = (const float*)sD;
+        const DomRec* sDom = (const DomRec*)(sD + Cf::DT_BYTES);
         const int nv = min(kTileDoms, g.nkept - t * kTileDoms);
-        const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * Cf::NKC * kTileDoms);
+        const bool dvalid = dl < nv;
+        // this lane's domain constants
+        const float nX = -sX[dl];
+        const float F0 = sX[kTileDoms + dl];
+        const float F1 = sX[2 * kTileDoms + dl];
+        const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * Cf::NKC * kTileRows);
 
         auto load = [&](int ch, uint32_t(&r)[32]) {
           if constexpr (Cf::NKC == 1) {
             ptx::tmem_ld32(tb + ch * 32, r);
           } else {
             ptx::tmem_ld16<0>(tb + ch * 16, r);
-            ptx::tmem_ld16<16>(tb + kTileDoms + ch * 16, r);
+            ptx::tmem_ld16<16>(tb + kTileRows + ch * 16, r);
           }
         };
 
-        // fast screen of one chunk: the minimum float score over its
-        // columns and S (masked past the tile's last kept domain)
-        auto screen = [&](const float* c, int c0, int nvc, auto masked) {
-          constexpr bool MK = decltype(masked)::value;
-          float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
+        // exact candidates of ranges of the chunk whose float screen passed
+        // in some lane: every flagged lane scores its pair exactly, the warp
+        // takes the lexicographic minimum, and the range's best and
+        // threshold follow it
+        auto slow = [&](const float* c, const float* cm, int ch, uint32_t fl) {
+          const DomRec dr = sDom[dl];
 #pragma unroll
-          for (int j = 0; j < CW; j += 4) {
-            const float4 X = *(const float4*)(sX + c0 + j);
-            const float2 y01 = __ffma2_rn(nw2, make_float2(X.x, X.y), make_float2(c[j], c[j + 1]));
-            const float2 y23 = __ffma2_rn(nw2, make_float2(X.z, X.w), make_float2(c[j + 2], c[j + 3]));
-            if constexpr (MODE == MODE_GRID) {
-              const float4 U = *(const float4*)(sF0 + c0 + j);
-              const float4 G = *(const float4*)(sF1 + c0 + j);
-              const float yy[4] = {y01.x, y01.y, y23.x, y23.y};
-              const float uu[4] = {U.x, U.y, U.z, U.w};
-              const float gg[4] = {G.x, G.y, G.z, G.w};
-              float sc[4];
+          for (int j = 0; j < RPC; ++j) {
+            const int r = ch * RPC + j;
+            const bool mine = (fl >> j) & 1u;
+            if (!__any_sync(0xffffffffu, mine)) continue;
+            int64_t be = INT64_MAX, bk = INT64_MAX;
+            if (mine) {
+              int kmax = 7;
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                float p = rintf(yy[u] * gg[u]);
-                p = fminf(fmaxf(p, 0.f), qf);
-                sc[u] = p * fmaf(p, uu[u], -yy[u]);
-                if constexpr (MK) sc[u] = j + u < nvc ? sc[u] : INFINITY;
-              }
-              m0 = ptx::fmin3(sc[0], sc[1], m0);
-              m1 = ptx::fmin3(sc[2], sc[3], m1);
-            } else {
-              const float4 F = *(const float4*)(sF0 + c0 + j);
-              float2 s01 = __ffma2_rn(np0, y01, make_float2(F.x, F.y));
-              float2 s23 = __ffma2_rn(np0, y23, make_float2(F.z, F.w));
-              if constexpr (MK) {
-                s01.x = j < nvc ? s01.x : INFINITY;
-                s01.y = j + 1 < nvc ? s01.y : INFINITY;
-                s23.x = j + 2 < nvc ? s23.x : INFINITY;
-                s23.y = j + 3 < nvc ? s23.y : INFINITY;
-              }
-              m0 = ptx::fmin3(s01.x, s01.y, m0);
-              m1 = ptx::fmin3(s23.x, s23.y, m1);
-              if constexpr (MODE == MODE_M2) {
-                const float4 F1 = *(const float4*)(sF1 + c0 + j);
-                float2 b01 = __ffma2_rn(np1, y01, make_float2(F1.x, F1.y));
-                float2 b23 = __ffma2_rn(np1, y23, make_float2(F1.z, F1.w));
-                if constexpr (MK) {
-                  b01.x = j < nvc ? b01.x : INFINITY;
-                  b01.y = j + 1 < nvc ? b01.y : INFINITY;
-                  b23.x = j + 2 < nvc ? b23.x : INFINITY;
-                  b23.y = j + 3 < nvc ? b23.y : INFINITY;
+              for (int k = 6; k >= 0; --k)
+                if (c[8 * j + k] == cm[j]) kmax = k;
+              const int64_t srp_r = (int64_t)(int)(w[r] * (float)n);
+              const int64_t C = ((int64_t)(int)cm[j] << LOGN) - srp_r * (int64_t)dr.sdp;
+              auto cand = [&](int64_t p, int si) {
+                const int64_t e = p * p * dr.v - 8 * p * qv * C;
+                const int64_t key = ((int64_t)dr.pos * 8 + (p > 0 ? kmax : 0)) * m_s + si;
+                if (e < be || (e == be && key < bk)) {
+                  be = e;
+                  bk = key;
                 }
-                m2 = ptx::fmin3(b01.x, b01.y, m2);
-                m3 = ptx::fmin3(b23.x, b23.y, m3);
-              }
-            }
-          }
-          return fminf(fminf(m0, m1), fminf(m2, m3));
-        };
-
-        // slow path: exact scores of every candidate of the chunk that can win.
-        // The lane marks its candidate columns (float score <= threshold) in
-        // bit masks, then scores only those exactly, reading their exact
-        // correlations back from its own column of the scratch.
-        auto slow = [&](const float* c, int c0, int nvc, float mn) {
-          if (mn <= thr) {
-            // the chunk's best float candidate is scored exactly below, so
-            // nothing more than 2 delta above it can win either
-            const float cut = fminf(thr, __fadd_ru(mn, 2.f * delta));
-            uint32_t mk0 = 0, mk1 = 0;
-#pragma unroll
-            for (int j = 0; j < CW; j += 2) {
-              const float2 X2 = *(const float2*)(sX + c0 + j);
-              const float2 y = __ffma2_rn(nw2, X2, make_float2(c[j], c[j + 1]));
+              };
               if constexpr (MODE == MODE_GRID) {
-                const float2 U = *(const float2*)(sF0 + c0 + j);
-                const float2 G = *(const float2*)(sF1 + c0 + j);
-                float pa = fminf(fmaxf(rintf(y.x * G.x), 0.f), qf);
-                float pb = fminf(fmaxf(rintf(y.y * G.y), 0.f), qf);
-                if (pa * fmaf(pa, U.x, -y.x) <= cut) mk0 |= 1u << j;
-                if (pb * fmaf(pb, U.y, -y.y) <= cut) mk0 |= 2u << j;
+                const float y = fmaf(nX, w[r], cm[j]);
+                const int pi = (int)fminf(fmaxf(rintf(y * F1), 0.f), qf);
+                for (int pp = max(pi - 1, 0); pp <= min(pi + 1, qv); ++pp) cand(pp, pp);
               } else {
-                const float2 F = *(const float2*)(sF0 + c0 + j);
-                const float2 s0 = __ffma2_rn(np0, y, F);
-                if (s0.x <= cut) mk0 |= 1u << j;
-                if (s0.y <= cut) mk0 |= 2u << j;
-                if constexpr (MODE == MODE_M2) {
-                  const float2 F1 = *(const float2*)(sF1 + c0 + j);
-                  const float2 s1 = __ffma2_rn(np1, y, F1);
-                  if (s1.x <= cut) mk1 |= 1u << j;
-                  if (s1.y <= cut) mk1 |= 2u << j;
-                }
+                cand(a.S.p[0], 0);
+                if constexpr (MODE == MODE_M2) cand(a.S.p[1], 1);
               }
             }
-            const uint32_t lim = nvc >= 32 ? 0xffffffffu : (1u << nvc) - 1u;
-            mk0 &= lim;
-            mk1 &= lim;
-            if (mk0 | mk1) {
 #pragma unroll
-              for (int j = 0; j < CW; ++j) scr[j * 32 + lane] = c[j];
-              while (mk0) {
-                const int j = __ffs(mk0) - 1;
-                mk0 &= mk0 - 1;
-                const int col = c0 + j;
-                const float cf = scr[j * 32 + lane];
-                if constexpr (MODE == MODE_GRID) {
-                  const float y = fmaf(-w, sX[col], cf);
-                  const int pi = (int)fminf(fmaxf(rintf(y * sF1[col]), 0.f), qf);
-                  for (int pp = max(pi - 1, 0); pp <= min(pi + 1, qv); ++pp)
-                    exact(sDom, col, cf, pp);
-                } else {
-                  exact(sDom, col, cf, 0);
-                }
-              }
-              while (mk1) {
-                const int j = __ffs(mk1) - 1;
-                mk1 &= mk1 - 1;
-                exact(sDom, c0 + j, scr[j * 32 + lane], 1);
+            for (int o = 16; o > 0; o >>= 1) {
+              const int64_t e2 = __shfl_xor_sync(0xffffffffu, be, o);
+              const int64_t k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+              if (e2 < be || (e2 == be && k2 < bk)) {
+                be = e2;
+                bk = k2;
               }
             }
-          }
-          __syncwarp();
-          // the 8 isometry rows of a range share the tightest threshold
-          float t8 = thr;
-          t8 = fminf(t8, __shfl_xor_sync(0xffffffffu, t8, 1));
-          t8 = fminf(t8, __shfl_xor_sync(0xffffffffu, t8, 2));
-          t8 = fminf(t8, __shfl_xor_sync(0xffffffffu, t8, 4));
-          if (valid) {
-            thr = t8;
-            if (improved) {
-              atomicMin(gth, thr_to_ord(thr));
-              improved = false;
+            // every lane holds the warp's best of this range now
+            const Cand cur = mybest[r];
+            if (be < cur.score || (be == cur.score && bk < cur.key)) {
+              const float to = thr_of(be, inv_up, inv_dn, sDelta[r]);
+              __syncwarp();
+              if (lane == 0) {
+                mybest[r] = Cand{be, bk};
+                if (to < sThr[r]) {
+                  sThr[r] = to;
+                  atomicMin(a.gthr + g.r0 + r, thr_to_ord(to));
+                }
+              }
+              __syncwarp();
+              thr[r] = fminf(thr[r], to);
             }
           }
         };
 
-        auto chunk = [&](int ch, const uint32_t* r) {
-          const int c0 = ch * CW;
+        auto chunk = [&](int ch, const uint32_t* rg) {
           float c[CW];
           if constexpr (Cf::NKC == 1) {
 #pragma unroll
-            for (int j = 0; j < CW; ++j) c[j] = __uint_as_float(r[j]);
+            for (int j = 0; j < CW; ++j) c[j] = __uint_as_float(rg[j]);
           } else {
 #pragma unroll
             for (int j = 0; j < CW; j += 2) {
               const float2 s2 =
-                  __fadd2_rn(make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])),
-                             make_float2(__uint_as_float(r[16 + j]), __uint_as_float(r[17 + j])));
+                  __fadd2_rn(make_float2(__uint_as_float(rg[j]), __uint_as_float(rg[j + 1])),
+                             make_float2(__uint_as_float(rg[16 + j]), __uint_as_float(rg[17 + j])));
               c[j] = s2.x;
               c[j + 1] = s2.y;
             }
           }
-          const int nvc = nv - c0;
-          const float mn = nvc >= CW ? screen(c, c0, nvc, std::false_type{})
-                                     : screen(c, c0, nvc, std::true_type{});
-          if (__any_sync(0xffffffffu, mn <= thr)) slow(c, c0, nvc, mn);
+          float cm[RPC];
+          uint32_t fl = 0;
+#pragma unroll
+          for (int j = 0; j < RPC; ++j) {
+            const int r = ch * RPC + j;
+            const float* v = c + 8 * j;
+            cm[j] = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
+                          ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
+            const float y = fmaf(nX, w[r], cm[j]);
+            float sc;
+            if constexpr (MODE == MODE_GRID) {
+              float p = rintf(y * F1);
+              p = fminf(fmaxf(p, 0.f), qf);
+              sc = p * fmaf(p, F0, -y);
+            } else if constexpr (MODE == MODE_M2) {
+              sc = fminf(fmaf(-p0f, y, F0), fmaf(-p1f, y, F1));
+            } else {
+              sc = fmaf(-p0f, y, F0);
+            }
+            fl |= (sc <= thr[r]) ? (1u << j) : 0u;
+          }
+          if (!dvalid) fl = 0;
+          if (__any_sync(0xffffffffu, fl != 0)) slow(c, cm, ch, fl);
         };
 
         if (ok) {
-          if constexpr (EG == 2) {
-            // two warps per sub-partition: overlap the next chunk's TMEM
-            // load with this chunk's scoring
-            uint32_t ra[32], rb[32];
-            load(0, ra);
+          // two TMEM loads in flight: the next chunk's with this chunk's work
+          uint32_t ra[32], rb[32];
+          load(0, ra);
 #pragma unroll
-            for (int ch = 0; ch < Cf::NCH; ch += 2) {
-              if (ch * CW >= nv) break;
-              ptx::tmem_wait(ra);
-              if ((ch + 1) * CW < nv) load(ch + 1, rb);
-              chunk(ch, ra);
-              if ((ch + 1) * CW >= nv) break;
-              ptx::tmem_wait(rb);
-              if (ch + 2 < Cf::NCH && (ch + 2) * CW < nv) load(ch + 2, ra);
-              chunk(ch + 1, rb);
-            }
-          } else {
-            // three warps per sub-partition hide the load latency
-#pragma unroll 1
-            for (int ch = 0; ch < Cf::NCH; ++ch) {
-              if (ch * CW >= nv) break;
-              uint32_t ra[32];
-              load(ch, ra);
-              ptx::tmem_wait(ra);
-              chunk(ch, ra);
-            }
+          for (int ch = 0; ch < Cf::NCH; ch += 2) {
+            ptx::tmem_wait(ra);
+            load(ch + 1, rb);
+            chunk(ch, ra);
+            ptx::tmem_wait(rb);
+            if (ch + 2 < Cf::NCH) load(ch + 2, ra);
+            chunk(ch + 1, rb);
           }
         }
         ptx::tc_fence_before();
@@ -594,24 +570,19 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           ptx::mbar_arrive(&d_empty[db]);
         }
       }
-      // merge the groups' bests of this row; group 0 writes the partial
-      if (h > 0) mrg[(h - 1) * kTileRows + row] = Cand{best_e, best_key};
-      ptx::named_bar_sync(1 + qd, 32 * EG);
-      if (h == 0) {
-#pragma unroll
-        for (int o2 = 0; o2 < EG - 1; ++o2) {
-          const Cand o = mrg[o2 * kTileRows + row];
-          if (o.score < best_e || (o.score == best_e && o.key < best_key)) {
-            best_e = o.score;
-            best_key = o.key;
-          }
+      // merge the warps' bests per range; one thread per range writes the
+      // item's partial
+      __syncwarp();
+      ptx::named_bar_sync(1, epi_threads);
+      if (ew == 0 && lane < kTileRanges) {
+        Cand best{INT64_MAX, INT64_MAX};
+        for (int o = 0; o < Cf::Wp::EPI_WARPS; ++o) {
+          const Cand x = wbest[o * kTileRanges + lane];
+          if (x.score < best.score || (x.score == best.score && x.key < best.key)) best = x;
         }
-        Cand out;
-        out.score = valid ? best_e : INT64_MAX;
-        out.key = valid ? best_key : INT64_MAX;
-        a.part[it * kTileRows + row] = out;
+        if (lane >= g.nr) best = Cand{INT64_MAX, INT64_MAX};
+        a.part[it * kTileRanges + lane] = best;
       }
-      ptx::named_bar_sync(1 + qd, 32 * EG);
     }
   }
 

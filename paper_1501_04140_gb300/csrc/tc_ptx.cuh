@@ -198,5 +198,12 @@ __device__ inline float fmin3(float a, float b, float c) {
   return d;
 }
 
+// Three-input maximum (sm_100 family).
+__device__ inline float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 }  // namespace ptx
 }  // namespace fic
