@@ -113,7 +113,7 @@ int pool_alloc(PoolLevel& pl) {
   rc |= pl.dom.reserve(sizeof(DomRec) * S);
   rc |= pl.domf.reserve(sizeof(float4) * S);
   rc |= pl.umax.reserve(16);
-  if (pl.want_tc) rc |= pl.bpack.reserve(sizeof(uint16_t) * S * pl.Kp);
+  if (pl.want_tc) rc |= pl.bpack.reserve((size_t)(S / kTileDoms) * tc_tile_bytes(pl.B));
   if (pl.want_f32) rc |= pl.b32.reserve(sizeof(float) * S * pl.n);
   rc |= pl.scan_scratch.reserve(sizeof(int32_t) * scan_scratch_blocks(P));
   rc |= pl.total.reserve(sizeof(int64_t) * 2);

@@ -29,6 +29,18 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // bounded mbarrier 
 constexpr uint32_t kStatusTimeout = 1u;
 constexpr uint32_t kStatusOverflow = 2u;
 
+// Tensor-path operand geometry.  K (= n) is padded to the MMA's K step of
+// 16.  At B <= 8 each 128-domain tile of the kept pool is one contiguous
+// block: the f16 operand (core-matrix layout), four float planes of 128
+// scoring constants, then 128 DomRec -- one bulk copy per tile.  At B = 16
+// the operand tiles stand alone and the records are separate arrays.
+__host__ __device__ constexpr int tc_kp(int B) { return B * B < 16 ? 16 : B * B; }
+__host__ __device__ constexpr int tc_op_bytes(int B) { return kTileDoms * tc_kp(B) * 2; }
+__host__ __device__ constexpr int tc_rec_bytes() { return 4 * kTileDoms * 4 + kTileDoms * 16; }
+__host__ __device__ constexpr int tc_tile_bytes(int B) {
+  return B <= 8 ? tc_op_bytes(B) + tc_rec_bytes() : tc_op_bytes(B);
+}
+
 // ---------------------------------------------------------------- images
 struct ImgDev {
   const uint8_t* pix;  // device pointer, row-major

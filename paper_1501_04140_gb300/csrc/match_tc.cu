@@ -33,9 +33,12 @@
 //               records;
 //   warp 1      allocates tensor memory and issues the MMAs (one thread);
 //   warps 2-3   idle (they complete the control warpgroup);
-//   warps 4-    epilogue, EG groups of four warps: each warp owns the 32 TMEM
-//               lanes = 32 domains of its quarter; the groups take turns on
-//               the tiles and merge their per-range bests per item.
+//   warps 4-11  epilogue, two groups of four warps: each warp owns the 32
+//               TMEM lanes = 32 domains of its quarter; the groups take turns
+//               on the tiles and merge their per-range bests per item.  At
+//               B <= 8 a warp moves its whole 128-column tile into registers
+//               and hands the accumulator back to the MMA before scoring, so
+//               four accumulators keep the tensor pipe ahead of the scoring.
 //
 // Screening.  The float score E' / (8 q n) = p^2 u - p y, with
 // u = V / (8 q n) and y = C / n = cmax - (sum r' / n) sum Ds', screens the
@@ -93,33 +96,40 @@ struct TcWarps {
 
 template <int B>
 struct TcCfg {
-  static constexpr int EG = B == 16 ? 2 : 3;          // epilogue warp groups
+  static constexpr int EG = 2;                        // epilogue warp groups
   using Wp = TcWarps<EG>;
   static constexpr int n = B * B;
-  static constexpr int Kp = n < 16 ? 16 : n;          // K padded to the MMA K step
+  static constexpr int Kp = tc_kp(B);                 // K padded to the MMA K step
   static constexpr int NKC = n > 128 ? n / 128 : 1;   // exact accumulators per tile
   static constexpr int KS = Kp / NKC;                 // K per pipeline stage
   static constexpr int KSTEPS = KS / 16;              // MMAs per stage
+  // B <= 8: one stage = one whole tile block (operand + scoring records),
+  // one bulk copy and one barrier per tile; B = 16: one stage per K half,
+  // the scoring records in a ring of their own
+  static constexpr bool UNI = B <= 8;
+  static constexpr int NA = UNI ? 2 : 1;              // range-tile buffers
   static constexpr int A_BYTES = kTileRows * Kp * 2;
-  static constexpr int ST_BYTES = kTileDoms * KS * 2;
-  static constexpr int NST = B == 16 ? 4 : B == 8 ? 6 : 8;   // operand stages
+  static constexpr int OP_BYTES = kTileDoms * KS * 2;
+  static constexpr int DT_BYTES = 4 * kTileDoms * 4;  // float planes {sum Ds', F0, F1, 0}
+  static constexpr int DR_BYTES = kTileDoms * 16;     // DomRec per domain
+  static constexpr int D_BYTES = DT_BYTES + DR_BYTES;
+  static constexpr int ST_BYTES = UNI ? OP_BYTES + D_BYTES : OP_BYTES;
+  static_assert(!UNI || ST_BYTES == tc_tile_bytes(B), "tile block layout");
+  static constexpr int NST = B == 16 ? 4 : B == 8 ? 8 : 16;  // stages
   static constexpr int NACC = B == 16 ? 2 : 4;                // TMEM accumulators
-  static constexpr int ND = B == 16 ? 4 : B == 8 ? 8 : 16;    // scoring-record stages
+  static constexpr int ND = UNI ? 0 : 4;                      // scoring-record stages (B = 16)
   static constexpr int TCOLS = 512;
   static constexpr int CW = NKC == 1 ? 32 : 16;       // tile columns per epilogue chunk
   static constexpr int RPC = CW / 8;                  // ranges per chunk
   static constexpr int NCH = kTileRows / CW;
-  static constexpr int DT_BYTES = 4 * kTileDoms * 4;  // float planes {sum Ds', F0, F1, 0}
-  static constexpr int DR_BYTES = kTileDoms * 16;     // DomRec per domain
-  static constexpr int D_BYTES = DT_BYTES + DR_BYTES;
   static constexpr int MRG_BYTES = Wp::EPI_WARPS * kTileRanges * 16;  // per-warp range bests
   static constexpr int SCR_BYTES = 3 * kTileRanges * 4;  // per range: w, delta, threshold
-  static constexpr int OFF_B = A_BYTES;
+  static constexpr int OFF_B = NA * A_BYTES;
   static constexpr int OFF_D = OFF_B + NST * ST_BYTES;
   static constexpr int OFF_MRG = OFF_D + ND * D_BYTES;
   static constexpr int OFF_SCR = OFF_MRG + MRG_BYTES;
   static constexpr int OFF_BAR = OFF_SCR + SCR_BYTES;
-  static constexpr int NBAR = 2 * NST + 2 + 2 * NACC + 2 * ND + 1;
+  static constexpr int NBAR = 2 * NST + 2 * NA + 2 * NACC + 2 * ND + 1;
   static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
   static constexpr int BYTES = OFF_MISC + 16;
   // one CTA per SM: the CTA owns all 512 TMEM columns
@@ -133,15 +143,21 @@ constexpr int MODE_M1 = 0, MODE_M2 = 1, MODE_GRID = 2;
 struct ItemGeo {
   int im, nr, t0, t1, nkept;
   int64_t r0, slot0;
+  int64_t pidx;  // index of the item's partials: (range tile) * chunks + chunk
 };
 
+// Items run chunk-major within an image: every range tile's first domain
+// chunk before any second chunk, so the later chunks of a range tile start
+// from the thresholds its earlier chunks published.
 __device__ inline ItemGeo item_geo(const MatchArgs& a, int64_t it, int CH) {
   ItemGeo g;
   g.im = find_segment(a.item_off, a.n_images, it);
   const int nc = a.chunks[g.im];
   const int64_t local = it - a.item_off[g.im];
-  const int64_t mt = local / nc;
-  const int c = (int)(local % nc);
+  const int64_t nmt = ceil_div64(a.act_cnt[g.im], kTileRanges);
+  const int c = (int)(local / nmt);
+  const int64_t mt = local % nmt;
+  g.pidx = a.item_off[g.im] + mt * nc + c;
   g.r0 = a.act_off[g.im] + mt * kTileRanges;
   g.nr = (int)min((int64_t)kTileRanges, a.act_cnt[g.im] - mt * kTileRanges);
   g.nkept = a.sel[g.im].nkept;
@@ -175,8 +191,8 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
   uint64_t* full_b = bars;
   uint64_t* empty_b = bars + Cf::NST;
   uint64_t* a_full = bars + 2 * Cf::NST;
-  uint64_t* a_empty = a_full + 1;
-  uint64_t* acc_full = a_empty + 1;
+  uint64_t* a_empty = a_full + Cf::NA;
+  uint64_t* acc_full = a_empty + Cf::NA;
   uint64_t* acc_empty = acc_full + Cf::NACC;
   uint64_t* d_full = acc_empty + Cf::NACC;
   uint64_t* d_empty = d_full + Cf::ND;
@@ -188,10 +204,14 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
   if (threadIdx.x == 0) {
     for (int i = 0; i < Cf::NST; ++i) {
       ptx::mbar_init(&full_b[i], 1);
-      ptx::mbar_init(&empty_b[i], 1);
+      // a whole-tile stage is released by the four epilogue warps that
+      // score it, a K-half stage by the MMA's commit
+      ptx::mbar_init(&empty_b[i], Cf::UNI ? 4 : 1);
     }
-    ptx::mbar_init(a_full, 1);
-    ptx::mbar_init(a_empty, 1);
+    for (int i = 0; i < Cf::NA; ++i) {
+      ptx::mbar_init(&a_full[i], 1);
+      ptx::mbar_init(&a_empty[i], 1);
+    }
     for (int i = 0; i < Cf::NACC; ++i) {
       ptx::mbar_init(&acc_full[i], 1);
       ptx::mbar_init(&acc_empty[i], 4);  // the four warps of the group that reads it
@@ -225,37 +245,38 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      uint32_t bi = 0, ai = 0, ti = 0;
-      uint32_t issued_par[Cf::NST], d_par[Cf::ND];
-      bool issued[Cf::NST], d_issued[Cf::ND];
-      for (int i = 0; i < Cf::NST; ++i) issued[i] = false, issued_par[i] = 0;
-      for (int i = 0; i < Cf::ND; ++i) d_issued[i] = false, d_par[i] = 0;
+      uint32_t si = 0, ai = 0, di = 0;  // stage, range-tile and record fills
       bool ok = true;
       for (int64_t it = blockIdx.x; ok && it < items; it += gridDim.x) {
         const ItemGeo g = item_geo(a, it, CH);
-        if (!ptx::mbar_wait(a_empty, (ai & 1) ^ 1) || *abort_flag) { ok = false; break; }
-        ptx::mbar_expect_tx(a_full, Cf::A_BYTES);
-        ptx::bulk_g2s(sA, a.apack + g.r0 * 8 * Cf::Kp, Cf::A_BYTES, a_full);
+        const int ab = ai % Cf::NA;
+        if (!ptx::mbar_wait(&a_empty[ab], ((ai / Cf::NA) & 1) ^ 1) || *abort_flag) {
+          ok = false;
+          break;
+        }
+        ptx::mbar_expect_tx(&a_full[ab], Cf::A_BYTES);
+        ptx::bulk_g2s(sA + ab * Cf::A_BYTES, a.apack + g.r0 * 8 * Cf::Kp, Cf::A_BYTES,
+                      &a_full[ab]);
         ++ai;
         for (int t = g.t0; ok && t < g.t1; ++t) {
-          // the tile's scoring records: a ring of their own, ND tiles ahead
-          const int db = ti % Cf::ND;
-          if (!ptx::mbar_wait(&d_empty[db], ((ti / Cf::ND) & 1) ^ 1) || *abort_flag) {
-            ok = false;
-            break;
-          }
           const int64_t tile_g = g.slot0 / kTileDoms + t;
-          uint8_t* dst = smem + Cf::OFF_D + db * Cf::D_BYTES;
-          ptx::mbar_expect_tx(&d_full[db], Cf::D_BYTES);
-          ptx::bulk_g2s(dst, a.domf + tile_g * (4 * kTileDoms), Cf::DT_BYTES, &d_full[db]);
-          ptx::bulk_g2s(dst + Cf::DT_BYTES, a.dom + tile_g * kTileDoms, Cf::DR_BYTES,
-                        &d_full[db]);
-          d_issued[db] = true;
-          d_par[db] = (ti / Cf::ND) & 1;
-          ++ti;
+          if constexpr (!Cf::UNI) {
+            // the tile's scoring records: a ring of their own, ND tiles ahead
+            const int db = di % Cf::ND;
+            if (!ptx::mbar_wait(&d_empty[db], ((di / Cf::ND) & 1) ^ 1) || *abort_flag) {
+              ok = false;
+              break;
+            }
+            uint8_t* dst = smem + Cf::OFF_D + db * Cf::D_BYTES;
+            ptx::mbar_expect_tx(&d_full[db], Cf::D_BYTES);
+            ptx::bulk_g2s(dst, a.domf + tile_g * (4 * kTileDoms), Cf::DT_BYTES, &d_full[db]);
+            ptx::bulk_g2s(dst + Cf::DT_BYTES, a.dom + tile_g * kTileDoms, Cf::DR_BYTES,
+                          &d_full[db]);
+            ++di;
+          }
           for (int kc = 0; kc < Cf::NKC; ++kc) {
-            const int st = bi % Cf::NST;
-            if (!ptx::mbar_wait(&empty_b[st], ((bi / Cf::NST) & 1) ^ 1) || *abort_flag) {
+            const int st = si % Cf::NST;
+            if (!ptx::mbar_wait(&empty_b[st], ((si / Cf::NST) & 1) ^ 1) || *abort_flag) {
               ok = false;
               break;
             }
@@ -263,40 +284,44 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
             ptx::bulk_g2s(sB + st * Cf::ST_BYTES,
                           (const uint8_t*)a.bpack + (tile_g * Cf::NKC + kc) * Cf::ST_BYTES,
                           Cf::ST_BYTES, &full_b[st]);
-            issued[st] = true;
-            issued_par[st] = (bi / Cf::NST) & 1;
-            ++bi;
+            ++si;
           }
         }
       }
       if (!ok) fail();
       // drain: every copy this thread issued has landed before the CTA exits
-      for (int i = 0; i < Cf::NST; ++i)
-        if (issued[i]) ptx::mbar_wait(&full_b[i], issued_par[i]);
-      for (int i = 0; i < Cf::ND; ++i)
-        if (d_issued[i]) ptx::mbar_wait(&d_full[i], d_par[i]);
+      // (the last fill of each buffer, fill f waits for parity (f / N) & 1)
+      for (uint32_t i = 0; i < Cf::NST; ++i)
+        if (si > i) ptx::mbar_wait(&full_b[i], ((i + (si - 1 - i) / Cf::NST * Cf::NST) / Cf::NST) & 1);
+      for (uint32_t i = 0; i < Cf::NA; ++i)
+        if (ai > i) ptx::mbar_wait(&a_full[i], ((i + (ai - 1 - i) / Cf::NA * Cf::NA) / Cf::NA) & 1);
+      if constexpr (Cf::ND > 0)
+        for (uint32_t i = 0; i < Cf::ND; ++i)
+          if (di > i) ptx::mbar_wait(&d_full[i], ((i + (di - 1 - i) / Cf::ND * Cf::ND) / Cf::ND) & 1);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t IDESC = ptx::idesc_f16_f32(kTileDoms, kTileRows);
-      uint32_t bi = 0, ai = 0, ti = 0;
+      uint32_t si = 0, ai = 0, ti = 0;
       bool ok = true;
       for (int64_t it = blockIdx.x; ok && it < items; it += gridDim.x) {
         const ItemGeo g = item_geo(a, it, CH);
-        if (!ptx::mbar_wait(a_full, ai & 1) || *abort_flag) { ok = false; break; }
-        ++ai;
-        ptx::tc_fence_after();
+        const int rb = ai % Cf::NA;
+        if (!ptx::mbar_wait(&a_full[rb], (ai / Cf::NA) & 1) || *abort_flag) {
+          ok = false;
+          break;
+        }
+        const uint8_t* sR = sA + rb * Cf::A_BYTES;
         for (int t = g.t0; ok && t < g.t1; ++t) {
           const int ab = ti % Cf::NACC;
           if (!ptx::mbar_wait(&acc_empty[ab], ((ti / Cf::NACC) & 1) ^ 1) || *abort_flag) {
             ok = false;
             break;
           }
-          ptx::tc_fence_after();
           for (int kc = 0; kc < Cf::NKC; ++kc) {
-            const int st = bi % Cf::NST;
-            if (!ptx::mbar_wait(&full_b[st], (bi / Cf::NST) & 1) || *abort_flag) {
+            const int st = si % Cf::NST;
+            if (!ptx::mbar_wait(&full_b[st], (si / Cf::NST) & 1) || *abort_flag) {
               ok = false;
               break;
             }
@@ -304,21 +329,22 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
             const uint32_t d = tmem + (uint32_t)((ab * Cf::NKC + kc) * kTileDoms);
 #pragma unroll
             for (int s = 0; s < Cf::KSTEPS; ++s) {
-              const int kk = (kc * Cf::KSTEPS + s) * 2;  // core-matrix column of A
+              const int kk = (kc * Cf::KSTEPS + s) * 2;  // core-matrix column of the range tile
               // A = the domain stage (one TMEM lane per domain), B = the
               // resident range tile (columns = range x isometry)
-              const uint64_t rd = ptx::smem_desc(sA + kk * 128, 128, 16 * Cf::Kp);
+              const uint64_t rd = ptx::smem_desc(sR + kk * 128, 128, 16 * Cf::Kp);
               const uint64_t dd = ptx::smem_desc(sB + st * Cf::ST_BYTES + s * 256, 128, 16 * Cf::KS);
               ptx::mma_f16(d, dd, rd, IDESC, s > 0 ? 1u : 0u);
             }
-            ptx::mma_commit(&empty_b[st]);
-            ++bi;
+            if constexpr (!Cf::UNI) ptx::mma_commit(&empty_b[st]);
+            ++si;
           }
           if (!ok) break;
           ptx::mma_commit(&acc_full[ab]);
           ++ti;
         }
-        ptx::mma_commit(a_empty);
+        ptx::mma_commit(&a_empty[rb]);
+        ++ai;
       }
       if (!ok) fail();
       ptx::mma_commit(done_bar);
@@ -400,9 +426,15 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       for (int t = g.t0; t < g.t1; ++t, ++ti) {
         if ((int)(ti % EG) != h) continue;
         const int ab = ti % Cf::NACC;
-        const int db = ti % Cf::ND;
+        // the tile's scoring records: in its whole-tile stage (B <= 8; one
+        // stage per tile, so stage fill = tile), or in the record ring
+        constexpr int NREC = Cf::UNI ? Cf::NST : Cf::ND;
+        const int db = ti % NREC;
+        uint64_t* rec_full = Cf::UNI ? &full_b[db] : &d_full[db];
+        uint64_t* rec_empty = Cf::UNI ? &empty_b[db] : &d_empty[db];
+        const uint32_t rec_par = (ti / NREC) & 1;
         const bool got = ok && ptx::mbar_wait(&acc_full[ab], (ti / Cf::NACC) & 1) &&
-                         ptx::mbar_wait(&d_full[db], (ti / Cf::ND) & 1);
+                         ptx::mbar_wait(rec_full, rec_par);
         // the TMEM loads below are warp-collective: the lanes agree on the outcome
         const bool all = __all_sync(0xffffffffu, got);
         if (ok && !all && lane == 0) fail();
@@ -426,7 +458,8 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           thr[r + 2] = fminf(thr[r + 2], tv.z);
           thr[r + 3] = fminf(thr[r + 3], tv.w);
         }
-        const uint8_t* sD = smem + Cf::OFF_D + db * Cf::D_BYTES;
+        const uint8_t* sD = Cf::UNI ? sB + db * Cf::ST_BYTES + Cf::OP_BYTES
+                                    : smem + Cf::OFF_D + db * Cf::D_BYTES;
         const float* sX = (const float*)sD;
         const DomRec* sDom = (const DomRec*)(sD + Cf::DT_BYTES);
         const int nv = min(kTileDoms, g.nkept - t * kTileDoms);
@@ -509,6 +542,26 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           }
         };
 
+        // float screen of one (domain, range) pair: the maximum of the range's
+        // 8 isometry correlations, then the best score over S against the
+        // range's threshold
+        auto screen = [&](const float* v, int r, float& cmax) -> uint32_t {
+          cmax = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
+                       ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
+          const float y = fmaf(nX, w[r], cmax);
+          float sc;
+          if constexpr (MODE == MODE_GRID) {
+            float p = rintf(y * F1);
+            p = fminf(fmaxf(p, 0.f), qf);
+            sc = p * fmaf(p, F0, -y);
+          } else if constexpr (MODE == MODE_M2) {
+            sc = fminf(fmaf(-p0f, y, F0), fmaf(-p1f, y, F1));
+          } else {
+            sc = fmaf(-p0f, y, F0);
+          }
+          return sc <= thr[r] ? 1u : 0u;
+        };
+
         auto chunk = [&](int ch, const uint32_t* rg) {
           float c[CW];
           if constexpr (Cf::NKC == 1) {
@@ -527,47 +580,86 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           float cm[RPC];
           uint32_t fl = 0;
 #pragma unroll
-          for (int j = 0; j < RPC; ++j) {
-            const int r = ch * RPC + j;
-            const float* v = c + 8 * j;
-            cm[j] = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
-                          ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
-            const float y = fmaf(nX, w[r], cm[j]);
-            float sc;
-            if constexpr (MODE == MODE_GRID) {
-              float p = rintf(y * F1);
-              p = fminf(fmaxf(p, 0.f), qf);
-              sc = p * fmaf(p, F0, -y);
-            } else if constexpr (MODE == MODE_M2) {
-              sc = fminf(fmaf(-p0f, y, F0), fmaf(-p1f, y, F1));
-            } else {
-              sc = fmaf(-p0f, y, F0);
-            }
-            fl |= (sc <= thr[r]) ? (1u << j) : 0u;
-          }
+          for (int j = 0; j < RPC; ++j) fl |= screen(c + 8 * j, ch * RPC + j, cm[j]) << j;
           if (!dvalid) fl = 0;
           if (__any_sync(0xffffffffu, fl != 0)) slow(c, cm, ch, fl);
         };
 
-        if (ok) {
-          // two TMEM loads in flight: the next chunk's with this chunk's work
-          uint32_t ra[32], rb[32];
-          load(0, ra);
-#pragma unroll
-          for (int ch = 0; ch < Cf::NCH; ch += 2) {
-            ptx::tmem_wait(ra);
-            load(ch + 1, rb);
-            chunk(ch, ra);
-            ptx::tmem_wait(rb);
-            if (ch + 2 < Cf::NCH) load(ch + 2, ra);
-            chunk(ch + 1, rb);
+        if constexpr (Cf::NKC == 1) {
+          // the whole 128-column tile into registers, then the accumulator
+          // goes back to the MMA before any scoring
+          uint32_t r0[32], r1[32], r2[32], r3[32];
+          if (ok) {
+            load(0, r0);
+            load(1, r1);
+            load(2, r2);
+            load(3, r3);
+            ptx::tmem_wait(r0);
+            ptx::tmem_dep(r1);
+            ptx::tmem_dep(r2);
+            ptx::tmem_dep(r3);
           }
-        }
-        ptx::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          ptx::mbar_arrive(&acc_empty[ab]);
-          ptx::mbar_arrive(&d_empty[db]);
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
+          if (ok) {
+            // screen all 16 ranges of the tile (independent chains, no
+            // branch), then one vote before any exact work
+            float cm[kTileRanges];
+            uint32_t fl = 0;
+            auto screen4 = [&](const uint32_t* rg, int ch) {
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                float v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(rg[8 * j + k]);
+                fl |= screen(v, ch * 4 + j, cm[ch * 4 + j]) << (ch * 4 + j);
+              }
+            };
+            screen4(r0, 0);
+            screen4(r1, 1);
+            screen4(r2, 2);
+            screen4(r3, 3);
+            if (!dvalid) fl = 0;
+            if (__any_sync(0xffffffffu, fl != 0)) {
+              auto slow4 = [&](const uint32_t* rg, int ch) {
+                const uint32_t f4 = (fl >> (4 * ch)) & 0xFu;
+                if (__any_sync(0xffffffffu, f4 != 0)) {
+                  float c[32];
+#pragma unroll
+                  for (int j = 0; j < 32; ++j) c[j] = __uint_as_float(rg[j]);
+                  slow(c, cm + 4 * ch, ch, f4);
+                }
+              };
+              slow4(r0, 0);
+              slow4(r1, 1);
+              slow4(r2, 2);
+              slow4(r3, 3);
+            }
+          }
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(rec_empty);
+        } else {
+          if (ok) {
+            // two TMEM loads in flight: the next chunk's with this chunk's work
+            uint32_t ra[32], rb[32];
+            load(0, ra);
+#pragma unroll
+            for (int ch = 0; ch < Cf::NCH; ch += 2) {
+              ptx::tmem_wait(ra);
+              load(ch + 1, rb);
+              chunk(ch, ra);
+              ptx::tmem_wait(rb);
+              if (ch + 2 < Cf::NCH) load(ch + 2, ra);
+              chunk(ch + 1, rb);
+            }
+          }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            ptx::mbar_arrive(&acc_empty[ab]);
+            ptx::mbar_arrive(rec_empty);
+          }
         }
       }
       // merge the warps' bests per range; one thread per range writes the
@@ -581,7 +673,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           if (x.score < best.score || (x.score == best.score && x.key < best.key)) best = x;
         }
         if (lane >= g.nr) best = Cand{INT64_MAX, INT64_MAX};
-        a.part[it * kTileRanges + lane] = best;
+        a.part[g.pidx * kTileRanges + lane] = best;
       }
     }
   }

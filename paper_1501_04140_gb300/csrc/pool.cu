@@ -247,7 +247,8 @@ __device__ inline uint16_t f16_bits(int v) {
 // K slice kc (one slice of 128 at B = 16, the whole padded K otherwise), the
 // tile's 16 groups of 8 domains, each as K/8 core matrices of 8 domains x 8
 // f16 (16-byte rows): [T][kc][group][k / 8][slot % 8][k % 8].  A (T, kc)
-// slice is contiguous and is copied to shared memory as it is.
+// slice is contiguous and is copied to shared memory as it is.  At B <= 8
+// the tile's operand is followed by its scoring records (tc_tile_bytes).
 template <int B>
 struct PackGeom {
   static constexpr int n = B * B;
@@ -292,15 +293,17 @@ k_pack_domains(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
     const int32_t pos = kept[slot];
     const int64_t gpos = off[im] + pos;
     const int x0 = (pos % I.px) * L, y0 = (pos / I.px) * L;
+    uint8_t* tile_blk = bpack ? (uint8_t*)bpack + (slot >> 7) * (int64_t)tc_tile_bytes(B) : nullptr;
+    uint16_t* tile_op = (uint16_t*)tile_blk;
     for (int c = gl; c < n; c += G) {
       const int ci = c / B, cj = c % B;
       const uint8_t* p = I.pix + (int64_t)(y0 + 2 * ci) * I.pitch + (x0 + 2 * cj);
       const int ds = p[0] + p[1] + p[I.pitch] + p[I.pitch + 1];
-      if (bpack) bpack[bpack_index<B>(slot, c)] = f16_bits(ds - 512);
+      if (bpack) tile_op[bpack_index<B>(slot & 127, c)] = f16_bits(ds - 512);
       if (b32) b32[slot * n + c] = (float)(ds - 512);
     }
     if (bpack && n < Kp)  // zero the K padding (B = 2: K = 4 of 16)
-      for (int c = n + gl; c < Kp; c += G) bpack[bpack_index<B>(slot, c)] = 0;
+      for (int c = n + gl; c < Kp; c += G) tile_op[bpack_index<B>(slot & 127, c)] = 0;
     if (gl == 0) {
       const int64_t s = sd[gpos], s2 = sq[gpos];
       DomRec r;
@@ -331,6 +334,14 @@ k_pack_domains(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
       ft[kTileDoms] = f0;
       ft[2 * kTileDoms] = f1;
       ft[3 * kTileDoms] = 0.0f;
+      if (B <= 8 && tile_blk) {  // the same records inside the tile block
+        float* fb = (float*)(tile_blk + tc_op_bytes(B)) + (slot & 127);
+        fb[0] = (float)r.sdp;
+        fb[kTileDoms] = f0;
+        fb[2 * kTileDoms] = f1;
+        fb[3 * kTileDoms] = 0.0f;
+        ((DomRec*)(tile_blk + tc_op_bytes(B) + 4 * kTileDoms * 4))[slot & 127] = r;
+      }
     }
   }
   __syncthreads();
