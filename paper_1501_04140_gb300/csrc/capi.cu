@@ -230,6 +230,10 @@ struct fic_code {
   // optional per-level events around the matcher and the whole level
   bool profile = false;
   cudaEvent_t ev[4][4] = {};
+  // the pools of levels 1.. depend on the images only: they are built on
+  // side streams forked from the encode's stream, off the level chain
+  cudaStream_t side[4] = {};
+  cudaEvent_t fork_ev = nullptr, pool_ev[4] = {};
 };
 
 struct fic_pool {
@@ -308,8 +312,10 @@ int level_alloc(fic_ctx* ctx, LevelWs& w, const std::vector<fic_image>& ims, int
 
 // Matching of the active ranges of one level against the level's pool,
 // then the exact map of every range (res).
+// With split >= 0 the reducer also takes the level's split decision (split =
+// 1 on the last level, which accepts every range).
 int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cudaStream_t st,
-                cudaEvent_t* ev = nullptr) {
+                cudaEvent_t* ev = nullptr, int split = -1) {
   PoolLevel& pl = w.pool;
   const int ni = pl.n_images;
   const bool tc = prm.precision == FIC_PREC_TENSOR;
@@ -321,7 +327,8 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
   const int grid = ctx->nsm;
   k_plan<<<1, 32, 0, st>>>(ni, w.act_off.as<int64_t>(), w.act_cnt.as<int64_t>(),
                            pl.sel.as<SelState>(), 4 * grid, w.item_cap, w.mt_cap,
-                           w.meta.as<PlanMeta>(), w.item_off.as<int64_t>(), w.chunks.as<int32_t>());
+                           w.meta.as<PlanMeta>(), w.item_off.as<int64_t>(), w.chunks.as<int32_t>(),
+                           w.acc_cnt.as<int32_t>(), w.rej_cnt.as<int32_t>());
   MatchArgs a{};
   a.B = w.B;
   a.n = w.n;
@@ -356,7 +363,9 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
                              pl.sel.as<SelState>(), w.item_off.as<int64_t>(),
                              w.chunks.as<int32_t>(), w.part.as<Cand>(), tc ? 1 : 8, pl.sset, level,
                              w.meta.as<PlanMeta>(), ctx->status.as<uint32_t>(),
-                             w.res.as<fic_transform>(), st);
+                             w.res.as<fic_transform>(), prm.rms_threshold, split > 0 ? 1 : 0,
+                             split >= 0 ? w.acc.as<uint8_t>() : nullptr, w.acc_cnt.as<int32_t>(),
+                             w.rej_cnt.as<int32_t>(), st);
 }
 
 int64_t ranges_at(const std::vector<fic_image>& ims, int B) {
@@ -392,6 +401,15 @@ int encode_device(fic_code* c, cudaStream_t st) {
   const int ni = c->n_images;
   const int B0 = prm.range_size0;
   int rc = FIC_OK;
+  // fork: the pools of levels 1.. on their side streams
+  if (c->n_levels > 1) {
+    FIC_CUDA_TRY(cudaEventRecord(c->fork_ev, st));
+    for (int l = 1; l < c->n_levels; ++l) {
+      FIC_CUDA_TRY(cudaStreamWaitEvent(c->side[l], c->fork_ev, 0));
+      if ((rc = pool_build(c->lv[l].pool, ctx->dT.as<int64_t>(), c->side[l]))) return rc;
+      FIC_CUDA_TRY(cudaEventRecord(c->pool_ev[l], c->side[l]));
+    }
+  }
   for (int l = 0; l < c->n_levels; ++l) {
     LevelWs& w = c->lv[l];
     PoolLevel& pl = w.pool;
@@ -403,12 +421,17 @@ int encode_device(fic_code* c, cudaStream_t st) {
                                           w.rec.as<RangeRec>(), w.n_act.as<int64_t>(),
                                           w.act_off.as<int64_t>(), w.act_cnt.as<int64_t>());
     }
-    if ((rc = pool_build(pl, ctx->dT.as<int64_t>(), st))) return rc;
-    if ((rc = level_match(ctx, w, prm, l, st, c->profile ? c->ev[l] : nullptr))) return rc;
+    if (l == 0) {
+      if ((rc = pool_build(pl, ctx->dT.as<int64_t>(), st))) return rc;
+    } else {
+      FIC_CUDA_TRY(cudaStreamWaitEvent(st, c->pool_ev[l], 0));  // join
+    }
     const bool last = (l == c->n_levels - 1);
+    if ((rc = level_match(ctx, w, prm, l, st, c->profile ? c->ev[l] : nullptr, last ? 1 : 0)))
+      return rc;
     LevelWs* nx = last ? nullptr : &c->lv[l + 1];
     rc = launch_split(w.res.as<fic_transform>(), w.rec.as<RangeRec>(), w.n_act.as<int64_t>(), w.cap,
-                      w.B, prm.rms_threshold, last ? 1 : 0, ni, w.acc.as<uint8_t>(),
+                      w.B, ni, w.acc.as<uint8_t>(),
                       w.acc_cnt.as<int32_t>(), w.rej_cnt.as<int32_t>(), w.code_off.as<int64_t>(),
                       w.codes.as<fic_transform>(), nx ? nx->rec.as<RangeRec>() : nullptr,
                       nx ? nx->act_off.as<int64_t>() : nullptr,
@@ -769,7 +792,12 @@ static int code_setup(fic_ctx* ctx, const fic_image* imgs, int n_images, const f
     int rc = level_alloc(ctx, w, c->dims, B, ranges_at(c->dims, B), *params);
     if (!rc) rc = pool_alloc(w.pool);
     if (rc) return rc;
+    if (l > 0) {
+      FIC_CUDA_TRY(cudaStreamCreateWithFlags(&c->side[l], cudaStreamNonBlocking));
+      FIC_CUDA_TRY(cudaEventCreateWithFlags(&c->pool_ev[l], cudaEventDisableTiming));
+    }
   }
+  if (c->n_levels > 1) FIC_CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
   return FIC_OK;
 }
 
@@ -935,6 +963,11 @@ void fic_code_free(fic_code* c) {
   for (auto& lv : c->ev)
     for (auto& e : lv)
       if (e) cudaEventDestroy(e);
+  for (int l = 0; l < 4; ++l) {
+    if (c->pool_ev[l]) cudaEventDestroy(c->pool_ev[l]);
+    if (c->side[l]) cudaStreamDestroy(c->side[l]);
+  }
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   for (auto& w : c->lv) w.release_all();
   c->rng_off.release();
   c->staging.buf.release();

@@ -3,11 +3,12 @@
 //                    T_k^-1(R) as matcher rows (f16 r - 128 and/or fp32);
 //   k_plan           work items (image, 16-range M tile, chunk of 128-domain
 //                    tiles) over a batch, from device-side counts;
-//   k_reduce_final   best candidate of every range over its 8 isometry rows
-//                    and all domain chunks, then Eq. 1 and Eq. 3 in exact
-//                    integers for the chosen map;
-//   k_split_*        accept when E <= n T^2 (last level: always), otherwise
-//                    split into four children (16 -> 8 -> 4 -> 2).
+//   k_reduce_final   best candidate of every range over all domain chunks
+//                    (and the 8 isometry rows of the FP32 path), then Eq. 1
+//                    and Eq. 3 in exact integers for the chosen map, and the
+//                    split decision: accept when E <= n T^2 (last level:
+//                    always), otherwise four children (16 -> 8 -> 4 -> 2);
+//   k_split_offsets + compaction   the saved codes and the next level's ranges.
 #include <math.h>
 
 #include "fic_internal.h"
@@ -113,8 +114,11 @@ int launch_range_pack(int B, const ImgDev* imgs, const RangeRec* rec, const int6
 __global__ void k_plan(int n_images, const int64_t* __restrict__ act_off,
                        const int64_t* __restrict__ act_cnt, const SelState* __restrict__ sel,
                        int target_items, int64_t item_cap, int64_t mt_cap, PlanMeta* meta,
-                       int64_t* __restrict__ item_off, int32_t* __restrict__ chunks) {
+                       int64_t* __restrict__ item_off, int32_t* __restrict__ chunks,
+                       int32_t* __restrict__ acc_cnt, int32_t* __restrict__ rej_cnt) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // the split counters of the level start at zero (k_reduce_final adds)
+  for (int i = 0; i < n_images; ++i) acc_cnt[i] = 0, rej_cnt[i] = 0;
   int64_t work = 0;
   for (int i = 0; i < n_images; ++i)
     work += ceil_div64(act_cnt[i], kTileRanges) * ceil_div64(sel[i].nkept, kTileDoms);
@@ -141,23 +145,35 @@ __global__ void k_plan(int n_images, const int64_t* __restrict__ act_off,
 }
 
 // ---------------------------------------------------------------- reduce + exact map
+// One warp per range: the lanes share the range's partial candidates (every
+// domain chunk, and the isometry rows of the FP32 path) and then the pixels
+// of the chosen pair; the exact moments are warp sums.  The split decision of
+// the quadtree (accept when E <= n T^2, the last level always) is taken here
+// as well, with per-image counts for the compaction that follows.
+constexpr int kReduceWarps = 8;
+
+__device__ inline void cand_min(Cand& b, const Cand& x) {
+  if (x.score < b.score || (x.score == b.score && x.key < b.key)) b = x;
+}
+
 template <int B>
-__global__ void k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec,
-                               const int64_t* __restrict__ n_act,
-                               const int64_t* __restrict__ act_off,
-                               const int64_t* __restrict__ pool_off, int n_images, int L,
-                               const SelState* __restrict__ sel,
-                               const int64_t* __restrict__ item_off,
-                               const int32_t* __restrict__ chunks, const Cand* __restrict__ part,
-                               int iso_rows, SSet S, int level,
-                               const PlanMeta* __restrict__ meta, uint32_t* __restrict__ status,
-                               fic_transform* __restrict__ res) {
+__global__ void __launch_bounds__(32 * kReduceWarps)
+k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec,
+               const int64_t* __restrict__ n_act, const int64_t* __restrict__ act_off,
+               const int64_t* __restrict__ pool_off, int n_images, int L,
+               const SelState* __restrict__ sel, const int64_t* __restrict__ item_off,
+               const int32_t* __restrict__ chunks, const Cand* __restrict__ part, int iso_rows,
+               SSet S, int level, const PlanMeta* __restrict__ meta, uint32_t* __restrict__ status,
+               fic_transform* __restrict__ res, double e_thr, int last, uint8_t* __restrict__ acc,
+               int32_t* __restrict__ acc_cnt, int32_t* __restrict__ rej_cnt) {
   constexpr int n = B * B;
+  const int lane = threadIdx.x & 31;
   const int64_t N = *n_act;
   const bool overflow = meta->overflow != 0;
   if (overflow && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusOverflow);
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
-       g += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t w0 = (int64_t)blockIdx.x * kReduceWarps + (threadIdx.x >> 5);
+  const int64_t wstep = (int64_t)gridDim.x * kReduceWarps;
+  for (int64_t g = w0; g < N; g += wstep) {
     const RangeRec r = rec[g];
     const int im = r.img;
     const int64_t l = g - act_off[im];
@@ -165,36 +181,34 @@ __global__ void k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* 
     const int rr = (int)(l % kTileRanges);
     const int nc = overflow ? 0 : chunks[im];
     Cand best{INT64_MAX, INT64_MAX};
-    for (int c = 0; c < nc; ++c) {
-      const Cand* p = part + ((item_off[im] + m * nc + c) * kTileRanges + rr) * iso_rows;
-      for (int k = 0; k < iso_rows; ++k) {
-        const Cand x = p[k];
-        if (x.score < best.score || (x.score == best.score && x.key < best.key)) best = x;
-      }
+    for (int e = lane; e < nc * iso_rows; e += 32) {
+      const int c = e / iso_rows, k = e % iso_rows;
+      cand_min(best, part[((item_off[im] + m * nc + c) * kTileRanges + rr) * iso_rows + k]);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      Cand x;
+      x.score = __shfl_xor_sync(0xffffffffu, best.score, o);
+      x.key = __shfl_xor_sync(0xffffffffu, best.key, o);
+      cand_min(best, x);
+    }
+    const ImgDev I = imgs[im];
+    const bool bad = best.key == INT64_MAX || best.key < 0 ||
+                     best.key / (8 * (int64_t)S.m) >= (int64_t)I.px * I.py;
     fic_transform t{};
     t.level = level;
     t.x = r.x;
     t.y = r.y;
     t.size = B;
-    const ImgDev I = imgs[im];
-    const bool bad = best.key == INT64_MAX || best.key < 0 ||
-                     best.key / (8 * (int64_t)S.m) >= (int64_t)I.px * I.py;
-    if (bad) {  // no candidate (plan overflow): flagged, never read as a map
-      t.dom_index = -1;
-      t.e = INFINITY;
-      t.e_num = INT64_MAX;
-      res[g] = t;
-      continue;
-    }
-    const int s_idx = (int)(best.key % S.m);
-    const int iso = (int)((best.key / S.m) % 8);
-    const int pos = (int)(best.key / (8 * (int64_t)S.m));
-    const int dx = (pos % I.px) * L, dy = (pos / I.px) * L;
-    // Exact moments of the chosen pair: Eq. 1 with D = Ds / 4 and s = p / q.
-    int64_t sr = 0, sr2 = 0, sdd = 0, sdd2 = 0, cor = 0;
-    for (int i = 0; i < B; ++i)
-      for (int j = 0; j < B; ++j) {
+    if (!bad) {
+      const int s_idx = (int)(best.key % S.m);
+      const int iso = (int)((best.key / S.m) % 8);
+      const int pos = (int)(best.key / (8 * (int64_t)S.m));
+      const int dx = (pos % I.px) * L, dy = (pos / I.px) * L;
+      // Exact moments of the chosen pair: Eq. 1 with D = Ds / 4 and s = p / q.
+      int64_t sr = 0, sr2 = 0, sdd = 0, sdd2 = 0, cor = 0;
+      for (int e = lane; e < n; e += 32) {
+        const int i = e / B, j = e % B;
         int si, sj;
         iso_src(B, iso, i, j, &si, &sj);
         const uint8_t* pd = I.pix + (int64_t)(dy + 2 * si) * I.pitch + (dx + 2 * sj);
@@ -206,25 +220,46 @@ __global__ void k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* 
         sdd2 += ds * ds;
         cor += rv * ds;
       }
-    const int64_t p = S.p[s_idx], q = S.q;
-    const int64_t A = n * sr2 - sr * sr;
-    const int64_t C = n * cor - sr * sdd;
-    const int64_t V = n * sdd2 - sdd * sdd;
-    // 16 q^2 n^2 E = n (16 q^2 A - 8 p q C + p^2 V)
-    const int64_t enum_ = (int64_t)n * (16 * q * q * A - 8 * p * q * C + p * p * V);
-    t.dom_index = pos;
-    t.dom_x = dx;
-    t.dom_y = dy;
-    t.iso = iso;
-    t.s_idx = s_idx;
-    t.p = (int32_t)p;
-    t.q = (int32_t)q;
-    t.e_num = enum_;
-    t.o_num = 4 * q * sr - p * sdd;  // Eq. 3 times 4 q n
-    t.e = (double)enum_ / (16.0 * (double)(q * q) * (double)n * (double)n);
-    t.s = (double)p / (double)q;
-    t.o = (double)t.o_num / (4.0 * (double)q * (double)n);
-    res[g] = t;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        sr2 += __shfl_xor_sync(0xffffffffu, sr2, o);
+        sdd += __shfl_xor_sync(0xffffffffu, sdd, o);
+        sdd2 += __shfl_xor_sync(0xffffffffu, sdd2, o);
+        cor += __shfl_xor_sync(0xffffffffu, cor, o);
+      }
+      const int64_t p = S.p[s_idx], q = S.q;
+      const int64_t A = n * sr2 - sr * sr;
+      const int64_t C = n * cor - sr * sdd;
+      const int64_t V = n * sdd2 - sdd * sdd;
+      // 16 q^2 n^2 E = n (16 q^2 A - 8 p q C + p^2 V)
+      const int64_t enum_ = (int64_t)n * (16 * q * q * A - 8 * p * q * C + p * p * V);
+      t.dom_index = pos;
+      t.dom_x = dx;
+      t.dom_y = dy;
+      t.iso = iso;
+      t.s_idx = s_idx;
+      t.p = (int32_t)p;
+      t.q = (int32_t)q;
+      t.e_num = enum_;
+      t.o_num = 4 * q * sr - p * sdd;  // Eq. 3 times 4 q n
+      t.e = (double)enum_ / (16.0 * (double)(q * q) * (double)n * (double)n);
+      t.s = (double)p / (double)q;
+      t.o = (double)t.o_num / (4.0 * (double)q * (double)n);
+    } else {  // no candidate (plan overflow): flagged, never read as a map
+      t.dom_index = -1;
+      t.e = INFINITY;
+      t.e_num = INT64_MAX;
+    }
+    if (lane == 0) {
+      res[g] = t;
+      if (acc) {
+        // Sec. 2: keep the map when its error is acceptable, else split
+        const bool a = last || (t.e <= e_thr);
+        acc[g] = a ? 1 : 0;
+        atomicAdd(a ? &acc_cnt[im] : &rej_cnt[im], 1);
+      }
+    }
   }
 }
 
@@ -233,15 +268,17 @@ int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const in
                         int n_images, int L, const SelState* sel, const int64_t* item_off,
                         const int32_t* chunks, const Cand* part, int iso_rows, const SSet& S,
                         int level, const PlanMeta* meta, uint32_t* status, fic_transform* res,
+                        double rms, int last, uint8_t* acc, int32_t* acc_cnt, int32_t* rej_cnt,
                         cudaStream_t st) {
-  const int threads = 128;
-  int grid = (int)ceil_div64(cap > 0 ? cap : 1, threads);
+  const int threads = 32 * kReduceWarps;
+  int grid = (int)ceil_div64(cap > 0 ? cap : 1, kReduceWarps);
   if (grid > 65535) grid = 65535;
-#define FIC_RF(BB)                                                                           \
-  k_reduce_final<BB><<<grid, threads, 0, st>>>(imgs, rec, n_act, act_off, pool_off, n_images, \
-                                               L, sel, item_off, chunks, part, iso_rows, S,  \
-                                               level, meta,                                   \
-                                               status, res)
+  const double e_thr = (double)(B * B) * (rms * rms);
+#define FIC_RF(BB)                                                                            \
+  k_reduce_final<BB><<<grid, threads, 0, st>>>(imgs, rec, n_act, act_off, pool_off, n_images,  \
+                                               L, sel, item_off, chunks, part, iso_rows, S,   \
+                                               level, meta, status, res, e_thr, last, acc,    \
+                                               acc_cnt, rej_cnt)
   switch (B) {
     case 16: FIC_RF(16); break;
     case 8: FIC_RF(8); break;
@@ -254,20 +291,10 @@ int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const in
 }
 
 // ---------------------------------------------------------------- quadtree split
-// Accept when E <= n T^2, compared in double as (double) e_num / (16 q^2 n^2)
-// against n (T T); the last level accepts everything.
-__global__ void k_split_flags(const fic_transform* __restrict__ res,
-                              const RangeRec* __restrict__ rec, const int64_t* __restrict__ n_act,
-                              double e_thr, int last, uint8_t* __restrict__ acc,
-                              int32_t* __restrict__ acc_cnt, int32_t* __restrict__ rej_cnt) {
-  const int64_t N = *n_act;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    const bool a = last || (res[g].e <= e_thr);
-    acc[g] = a ? 1 : 0;
-    atomicAdd(a ? &acc_cnt[rec[g].img] : &rej_cnt[rec[g].img], 1);
-  }
-}
+// (The accept / split flags and their per-image counts come from
+// k_reduce_final: accept when E <= n T^2, compared in double as
+// (double) e_num / (16 q^2 n^2) against n (T T); the last level accepts
+// everything.)
 
 // Per-image offsets of the codes saved at this level and of the next level's
 // ranges (4 children per split range); images stay in order.
@@ -314,17 +341,10 @@ struct SplitCompact {
 };
 
 int launch_split(const fic_transform* res, const RangeRec* rec, const int64_t* n_act, int64_t cap,
-                 int B, double rms, int last, int n_images, uint8_t* acc, int32_t* acc_cnt,
+                 int B, int n_images, uint8_t* acc, int32_t* acc_cnt,
                  int32_t* rej_cnt, int64_t* code_off, fic_transform* codes, RangeRec* next,
                  int64_t* next_off, int64_t* next_cnt, int64_t* next_n, int32_t* scan_scratch,
                  int64_t* total, cudaStream_t st) {
-  const int n = B * B;
-  const double e_thr = (double)n * (rms * rms);
-  cudaMemsetAsync(acc_cnt, 0, sizeof(int32_t) * n_images, st);
-  cudaMemsetAsync(rej_cnt, 0, sizeof(int32_t) * n_images, st);
-  int grid = (int)ceil_div64(cap > 0 ? cap : 1, 256);
-  if (grid > 65535) grid = 65535;
-  k_split_flags<<<grid, 256, 0, st>>>(res, rec, n_act, e_thr, last, acc, acc_cnt, rej_cnt);
   k_split_offsets<<<1, 32, 0, st>>>(n_images, acc_cnt, rej_cnt, code_off, next_off, next_cnt,
                                      next_n);
   SplitCompact sc{n_act, acc, res, rec, codes, next, B / 2};

@@ -13,6 +13,8 @@
 //                   plus the per-domain moments the scoring needs.
 #include <math.h>
 
+#include <algorithm>
+
 #include "fic_internal.h"
 #include "scan.cuh"
 
@@ -217,6 +219,78 @@ __global__ void k_sel_bases(SelState* st, int n_images) {
   }
 }
 
+// The same selection and the stable compaction of the kept positions in one
+// block per image, for pools of at most kSelFusedMax positions: the five
+// digit passes run over the image's keys from L2 with the histogram in
+// shared memory, then each thread compacts a contiguous run of positions.
+constexpr int kSelFusedThreads = 1024;
+constexpr int64_t kSelFusedMax = (int64_t)1 << 20;
+
+__global__ void __launch_bounds__(kSelFusedThreads)
+k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ off,
+                 const int64_t* __restrict__ slot_off, double pct, SelState* __restrict__ st,
+                 int32_t* __restrict__ kept, unsigned int* __restrict__ umax) {
+  __shared__ uint32_t hist[kSelBins];
+  __shared__ int sw[32];
+  __shared__ SelState s_st;
+  const int im = blockIdx.x;
+  const int64_t o0 = off[im], P = off[im + 1] - o0;
+  const int64_t* k = keys + o0;
+  if (threadIdx.x == 0) {
+    int64_t ih = (int64_t)floor(pct * (double)(P - 1));
+    if (ih < 0) ih = 0;
+    if (ih > P - 1) ih = P - 1;
+    SelState z{};
+    z.rank = (P > 0) ? (P - 1 - ih) : 0;
+    s_st = z;
+    if (im == 0) *umax = 0;  // the packer's running maximum starts here
+  }
+  for (int pass = 0; pass < kSelPasses; ++pass) {
+    const int shift = (kSelPasses - 1 - pass) * kSelBits;
+    for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    // every thread reads the state before the one that owns the digit
+    // rewrites it below
+    const int64_t prefix = s_st.prefix, rank = s_st.rank;
+#pragma unroll 4
+    for (int64_t g = threadIdx.x; g < P; g += blockDim.x) {
+      const int64_t kk = k[g];
+      if ((kk >> (shift + kSelBits)) == prefix) atomicAdd(&hist[(kk >> shift) & (kSelBins - 1)], 1u);
+    }
+    __syncthreads();
+    const int c = threadIdx.x < kSelBins ? (int)hist[threadIdx.x] : 0;
+    int tot;
+    const int before = block_excl_scan(c, sw, &tot);
+    if (threadIdx.x < kSelBins && tot > 0 && before <= rank && rank < before + c) {
+      SelState x = s_st;
+      x.prefix = (prefix << kSelBits) | threadIdx.x;
+      x.rank = rank - before;
+      x.nlt += before;
+      if (pass == kSelPasses - 1) {
+        x.thr = x.prefix;
+        x.nle = x.nlt + c;
+        x.fallback = (x.nlt == 0) ? 1 : 0;
+        x.nkept = (int32_t)(x.fallback ? x.nle : x.nlt);
+      }
+      s_st = x;
+    }
+    __syncthreads();
+  }
+  // stable compaction: kept = key below the threshold (or equal, fallback)
+  const int64_t thr = s_st.thr;
+  const bool fb = s_st.fallback != 0;
+  const int64_t chunk = ceil_div64(P, blockDim.x);
+  const int64_t g0 = (int64_t)threadIdx.x * chunk, g1 = min(P, g0 + chunk);
+  int cnt = 0;
+  for (int64_t g = g0; g < g1; ++g) cnt += fb ? (k[g] <= thr) : (k[g] < thr);
+  int tot;
+  int r = block_excl_scan(cnt, sw, &tot);
+  int32_t* out = kept + slot_off[im];
+  for (int64_t g = g0; g < g1; ++g)
+    if (fb ? (k[g] <= thr) : (k[g] < thr)) out[r++] = (int32_t)g;
+  if (threadIdx.x == 0) st[im] = s_st;
+}
+
 struct KeptCompact {
   const int64_t* keys;
   const int64_t* off;
@@ -379,20 +453,28 @@ int pool_build(PoolLevel& pl, const int64_t* d_dT, cudaStream_t st) {
   SelState* sel = pl.sel.as<SelState>();
   uint32_t* hist = pl.hist.as<uint32_t>();
   const int64_t* off = pl.off.as<int64_t>();
-  k_sel_init<<<ceil_div(ni * kSelBins, 256), 256, 0, st>>>(off, ni, pct, sel, hist);
-  const int nb = (int)ceil_div64(P > 0 ? P : 1, (int64_t)kSelThreads * kSelPerThread);
-  for (int pass = 0; pass < kSelPasses; ++pass) {
-    const int shift = (kSelPasses - 1 - pass) * kSelBits;
-    k_sel_hist<<<nb, kSelThreads, 0, st>>>(pl.keys.as<int64_t>(), off, ni, shift, sel, hist);
-    k_sel_find<<<ni, kSelBins, 0, st>>>(sel, hist, pass == kSelPasses - 1);
+  int64_t pmax = 0;
+  for (int i = 0; i < ni; ++i) pmax = std::max(pmax, pl.h_off[i + 1] - pl.h_off[i]);
+  if (pmax <= kSelFusedMax) {
+    k_select_compact<<<ni, kSelFusedThreads, 0, st>>>(pl.keys.as<int64_t>(), off,
+                                                      pl.slot_off.as<int64_t>(), pct, sel,
+                                                      pl.kept.as<int32_t>(), pl.umax.as<unsigned int>());
+  } else {
+    k_sel_init<<<ceil_div(ni * kSelBins, 256), 256, 0, st>>>(off, ni, pct, sel, hist);
+    const int nb = (int)ceil_div64(P > 0 ? P : 1, (int64_t)kSelThreads * kSelPerThread);
+    for (int pass = 0; pass < kSelPasses; ++pass) {
+      const int shift = (kSelPasses - 1 - pass) * kSelBits;
+      k_sel_hist<<<nb, kSelThreads, 0, st>>>(pl.keys.as<int64_t>(), off, ni, shift, sel, hist);
+      k_sel_find<<<ni, kSelBins, 0, st>>>(sel, hist, pass == kSelPasses - 1);
+    }
+    k_sel_bases<<<1, 32, 0, st>>>(sel, ni);
+    KeptCompact kc{pl.keys.as<int64_t>(), off, pl.slot_off.as<int64_t>(), sel,
+                   pl.kept.as<int32_t>(), ni};
+    FIC_CUDA_TRY(scan_compact(kc, P, pl.scan_scratch.as<int32_t>(), pl.total.as<int64_t>(), st));
+    FIC_CUDA_TRY(cudaMemsetAsync(pl.umax.p, 0, sizeof(unsigned int), st));
   }
-  k_sel_bases<<<1, 32, 0, st>>>(sel, ni);
-  KeptCompact kc{pl.keys.as<int64_t>(), off, pl.slot_off.as<int64_t>(), sel,
-                 pl.kept.as<int32_t>(), ni};
-  FIC_CUDA_TRY(scan_compact(kc, P, pl.scan_scratch.as<int32_t>(), pl.total.as<int64_t>(), st));
 
   const int nsm = pl.nsm > 0 ? pl.nsm : 148;
-  FIC_CUDA_TRY(cudaMemsetAsync(pl.umax.p, 0, sizeof(unsigned int), st));
   uint16_t* bp = pl.want_tc ? pl.bpack.as<uint16_t>() : nullptr;
   float* b32 = pl.want_f32 ? pl.b32.as<float>() : nullptr;
 #define FIC_PACK(BB)                                                                           \
