@@ -793,7 +793,10 @@ static int code_setup(fic_ctx* ctx, const fic_image* imgs, int n_images, const f
     if (!rc) rc = pool_alloc(w.pool);
     if (rc) return rc;
     if (l > 0) {
-      FIC_CUDA_TRY(cudaStreamCreateWithFlags(&c->side[l], cudaStreamNonBlocking));
+      // lowest priority: the level chain's own kernels go first
+      int lo = 0, hi = 0;
+      FIC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      FIC_CUDA_TRY(cudaStreamCreateWithPriority(&c->side[l], cudaStreamNonBlocking, lo));
       FIC_CUDA_TRY(cudaEventCreateWithFlags(&c->pool_ev[l], cudaEventDisableTiming));
     }
   }

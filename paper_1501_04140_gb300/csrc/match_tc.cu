@@ -33,12 +33,11 @@
 //               records;
 //   warp 1      allocates tensor memory and issues the MMAs (one thread);
 //   warps 2-3   idle (they complete the control warpgroup);
-//   warps 4-11  epilogue, two groups of four warps: each warp owns the 32
-//               TMEM lanes = 32 domains of its quarter; the groups take turns
-//               on the tiles and merge their per-range bests per item.  At
-//               B <= 8 a warp moves its whole 128-column tile into registers
-//               and hands the accumulator back to the MMA before scoring, so
-//               four accumulators keep the tensor pipe ahead of the scoring.
+//   warps 4-    epilogue, EG groups of four warps (four at B <= 8, two at
+//               B = 16): each warp owns the 32 TMEM lanes = 32 domains of its
+//               quarter; the groups take turns on the tiles and merge their
+//               per-range bests per item.  A warp hands its accumulator back
+//               to the MMA as soon as the tile's last chunk is in registers.
 //
 // Screening.  The float score E' / (8 q n) = p^2 u - p y, with
 // u = V / (8 q n) and y = C / n = cmax - (sum r' / n) sum Ds', screens the
@@ -87,16 +86,16 @@ template <int EG>
 struct TcWarps {
   static constexpr int EPI_WARPS = 4 * EG;  // EG warps per TMEM lane quarter
   static constexpr int THREADS = 32 * (kCtlWarps + EPI_WARPS);
-  static constexpr int LREGS = EG == 2 ? 168 : 128;
+  static constexpr int LREGS = EG == 2 ? 168 : EG == 3 ? 128 : 96;
   static constexpr int CREGS = EG == 2 ? 40 : 32;
-  static constexpr int EREGS = EG == 2 ? 232 : 160;
+  static constexpr int EREGS = EG == 2 ? 232 : EG == 3 ? 160 : 112;
   static_assert(32 * (kCtlWarps * CREGS + EPI_WARPS * EREGS) <= THREADS * LREGS,
                 "register split exceeds the launch budget");
 };
 
 template <int B>
 struct TcCfg {
-  static constexpr int EG = 2;                        // epilogue warp groups
+  static constexpr int EG = B == 16 ? 2 : 4;          // epilogue warp groups
   using Wp = TcWarps<EG>;
   static constexpr int n = B * B;
   static constexpr int Kp = tc_kp(B);                 // K padded to the MMA K step
@@ -362,9 +361,12 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
     // any CTA has published) in shared memory; the warps share their
     // threshold improvements there (a plain store of a smaller value: a lost
     // race only leaves a looser, still valid, threshold) and publish them to
-    // the other CTAs with atomicMin.
+    // the other CTAs with atomicMin.  At B <= 8 the warps read w and the
+    // thresholds from shared memory for every chunk; at B = 16 they keep
+    // register copies.
     constexpr int RPC = Cf::RPC;
     constexpr int REFRESH = 4;               // tiles between reads of the global thresholds
+    constexpr int RW = Cf::UNI ? 1 : kTileRanges;
     const int ew = warp - kCtlWarps;
     const int h = ew >> 2;
     const int qd = warp & 3;
@@ -412,13 +414,15 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       ptx::named_bar_sync(1, epi_threads);
       if (lane < kTileRanges) mybest[lane] = Cand{INT64_MAX, INT64_MAX};
       __syncwarp();
-      float w[kTileRanges], thr[kTileRanges];
+      float w[RW], thr[RW];
+      if constexpr (!Cf::UNI) {
 #pragma unroll
-      for (int r = 0; r < kTileRanges; r += 4) {
-        const float4 wv = *(const float4*)(sW + r);
-        const float4 tv = *(const float4*)(sThr + r);
-        w[r] = wv.x, w[r + 1] = wv.y, w[r + 2] = wv.z, w[r + 3] = wv.w;
-        thr[r] = tv.x, thr[r + 1] = tv.y, thr[r + 2] = tv.z, thr[r + 3] = tv.w;
+        for (int r = 0; r < kTileRanges; r += 4) {
+          const float4 wv = *(const float4*)(sW + r);
+          const float4 tv = *(const float4*)(sThr + r);
+          w[r] = wv.x, w[r + 1] = wv.y, w[r + 2] = wv.z, w[r + 3] = wv.w;
+          thr[r] = tv.x, thr[r + 1] = tv.y, thr[r + 2] = tv.z, thr[r + 3] = tv.w;
+        }
       }
       uint32_t gpre = rv ? __ldcg(a.gthr + g.r0 + rl) : kThrInit;
       int nmine = 0;
@@ -440,9 +444,8 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
         if (ok && !all && lane == 0) fail();
         ok = all;
         ptx::tc_fence_after();
-        // thresholds of the other warps (shared memory, every tile) and of
-        // the other CTAs (global, loaded REFRESH tiles ahead, passed on
-        // through shared memory)
+        // thresholds of the other CTAs: loaded REFRESH tiles ahead, passed on
+        // through shared memory
         if (++nmine % REFRESH == 0) {
           if (lane < kTileRanges && rv) {
             const float tg = ord_to_thr(gpre);
@@ -450,13 +453,15 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           }
           gpre = rv ? __ldcg(a.gthr + g.r0 + rl) : kThrInit;
         }
+        if constexpr (!Cf::UNI) {
 #pragma unroll
-        for (int r = 0; r < kTileRanges; r += 4) {
-          const float4 tv = *(const float4*)(sThr + r);
-          thr[r] = fminf(thr[r], tv.x);
-          thr[r + 1] = fminf(thr[r + 1], tv.y);
-          thr[r + 2] = fminf(thr[r + 2], tv.z);
-          thr[r + 3] = fminf(thr[r + 3], tv.w);
+          for (int r = 0; r < kTileRanges; r += 4) {
+            const float4 tv = *(const float4*)(sThr + r);
+            thr[r] = fminf(thr[r], tv.x);
+            thr[r + 1] = fminf(thr[r + 1], tv.y);
+            thr[r + 2] = fminf(thr[r + 2], tv.z);
+            thr[r + 3] = fminf(thr[r + 3], tv.w);
+          }
         }
         const uint8_t* sD = Cf::UNI ? sB + db * Cf::ST_BYTES + Cf::OP_BYTES
                                     : smem + Cf::OFF_D + db * Cf::D_BYTES;
@@ -479,76 +484,13 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           }
         };
 
-        // exact candidates of ranges of the chunk whose float screen passed
-        // in some lane: every flagged lane scores its pair exactly, the warp
-        // takes the lexicographic minimum, and the range's best and
-        // threshold follow it
-        auto slow = [&](const float* c, const float* cm, int ch, uint32_t fl) {
-          const DomRec dr = sDom[dl];
-#pragma unroll
-          for (int j = 0; j < RPC; ++j) {
-            const int r = ch * RPC + j;
-            const bool mine = (fl >> j) & 1u;
-            if (!__any_sync(0xffffffffu, mine)) continue;
-            int64_t be = INT64_MAX, bk = INT64_MAX;
-            if (mine) {
-              int kmax = 7;
-#pragma unroll
-              for (int k = 6; k >= 0; --k)
-                if (c[8 * j + k] == cm[j]) kmax = k;
-              const int64_t srp_r = (int64_t)(int)(w[r] * (float)n);
-              const int64_t C = ((int64_t)(int)cm[j] << LOGN) - srp_r * (int64_t)dr.sdp;
-              auto cand = [&](int64_t p, int si) {
-                const int64_t e = p * p * dr.v - 8 * p * qv * C;
-                const int64_t key = ((int64_t)dr.pos * 8 + (p > 0 ? kmax : 0)) * m_s + si;
-                if (e < be || (e == be && key < bk)) {
-                  be = e;
-                  bk = key;
-                }
-              };
-              if constexpr (MODE == MODE_GRID) {
-                const float y = fmaf(nX, w[r], cm[j]);
-                const int pi = (int)fminf(fmaxf(rintf(y * F1), 0.f), qf);
-                for (int pp = max(pi - 1, 0); pp <= min(pi + 1, qv); ++pp) cand(pp, pp);
-              } else {
-                cand(a.S.p[0], 0);
-                if constexpr (MODE == MODE_M2) cand(a.S.p[1], 1);
-              }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-              const int64_t e2 = __shfl_xor_sync(0xffffffffu, be, o);
-              const int64_t k2 = __shfl_xor_sync(0xffffffffu, bk, o);
-              if (e2 < be || (e2 == be && k2 < bk)) {
-                be = e2;
-                bk = k2;
-              }
-            }
-            // every lane holds the warp's best of this range now
-            const Cand cur = mybest[r];
-            if (be < cur.score || (be == cur.score && bk < cur.key)) {
-              const float to = thr_of(be, inv_up, inv_dn, sDelta[r]);
-              __syncwarp();
-              if (lane == 0) {
-                mybest[r] = Cand{be, bk};
-                if (to < sThr[r]) {
-                  sThr[r] = to;
-                  atomicMin(a.gthr + g.r0 + r, thr_to_ord(to));
-                }
-              }
-              __syncwarp();
-              thr[r] = fminf(thr[r], to);
-            }
-          }
-        };
-
         // float screen of one (domain, range) pair: the maximum of the range's
         // 8 isometry correlations, then the best score over S against the
         // range's threshold
-        auto screen = [&](const float* v, int r, float& cmax) -> uint32_t {
+        auto screen = [&](const float* v, float wr, float tr, float& cmax) -> uint32_t {
           cmax = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
                        ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
-          const float y = fmaf(nX, w[r], cmax);
+          const float y = fmaf(nX, wr, cmax);
           float sc;
           if constexpr (MODE == MODE_GRID) {
             float p = rintf(y * F1);
@@ -559,15 +501,124 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           } else {
             sc = fmaf(-p0f, y, F0);
           }
-          return sc <= thr[r] ? 1u : 0u;
+          return sc <= tr ? 1u : 0u;
         };
 
-        auto chunk = [&](int ch, const uint32_t* rg) {
-          float c[CW];
-          if constexpr (Cf::NKC == 1) {
+        // exact score of this lane's pair: the isometry with the largest
+        // correlation (k = 0 where p = 0), every s that can win
+        auto pair_exact = [&](const float* v, float cmax, float wr, const DomRec& dr,
+                              int64_t& be, int64_t& bk) {
+          int kmax = 7;
 #pragma unroll
-            for (int j = 0; j < CW; ++j) c[j] = __uint_as_float(rg[j]);
+          for (int k = 6; k >= 0; --k)
+            if (v[k] == cmax) kmax = k;
+          const int64_t srp_r = (int64_t)(int)(wr * (float)n);
+          const int64_t C = ((int64_t)(int)cmax << LOGN) - srp_r * (int64_t)dr.sdp;
+          auto cand = [&](int64_t p, int si) {
+            const int64_t e = p * p * dr.v - 8 * p * qv * C;
+            const int64_t key = ((int64_t)dr.pos * 8 + (p > 0 ? kmax : 0)) * m_s + si;
+            if (e < be || (e == be && key < bk)) {
+              be = e;
+              bk = key;
+            }
+          };
+          if constexpr (MODE == MODE_GRID) {
+            const float y = fmaf(nX, wr, cmax);
+            const int pi = (int)fminf(fmaxf(rintf(y * F1), 0.f), qf);
+            for (int pp = max(pi - 1, 0); pp <= min(pi + 1, qv); ++pp) cand(pp, pp);
           } else {
+            cand(a.S.p[0], 0);
+            if constexpr (MODE == MODE_M2) cand(a.S.p[1], 1);
+          }
+        };
+
+        // the warp's lexicographic minimum of range r's flagged pairs, then
+        // this warp's best of r and the shared thresholds; returns the new
+        // threshold (+inf if nothing improved)
+        auto resolve = [&](int r, int64_t be, int64_t bk) -> float {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const int64_t e2 = __shfl_xor_sync(0xffffffffu, be, o);
+            const int64_t k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+            if (e2 < be || (e2 == be && k2 < bk)) {
+              be = e2;
+              bk = k2;
+            }
+          }
+          // every lane holds the warp's best of this range now
+          const Cand cur = mybest[r];
+          float to = INFINITY;
+          if (be < cur.score || (be == cur.score && bk < cur.key)) {
+            to = thr_of(be, inv_up, inv_dn, sDelta[r]);
+            __syncwarp();
+            if (lane == 0) {
+              mybest[r] = Cand{be, bk};
+              if (to < sThr[r]) {
+                sThr[r] = to;
+                atomicMin(a.gthr + g.r0 + r, thr_to_ord(to));
+              }
+            }
+            __syncwarp();
+          }
+          return to;
+        };
+
+        if constexpr (Cf::UNI) {
+          // 32-column chunks = 4 ranges, two TMEM loads in flight; the
+          // accumulator goes back to the MMA once the last chunk is in
+          // registers
+          auto chunk = [&](int ch, const uint32_t* rg) {
+            const float4 wv4 = *(const float4*)(sW + 4 * ch);
+            const float4 tv4 = *(const float4*)(sThr + 4 * ch);
+            const float wr[4] = {wv4.x, wv4.y, wv4.z, wv4.w};
+            const float tr[4] = {tv4.x, tv4.y, tv4.z, tv4.w};
+            float c[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) c[j] = __uint_as_float(rg[j]);
+            float cm[4];
+            uint32_t fl = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) fl |= screen(c + 8 * j, wr[j], tr[j], cm[j]) << j;
+            if (!dvalid) fl = 0;
+            if (__any_sync(0xffffffffu, fl != 0)) {
+              const DomRec dr = sDom[dl];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const bool mine = (fl >> j) & 1u;
+                if (!__any_sync(0xffffffffu, mine)) continue;
+                int64_t be = INT64_MAX, bk = INT64_MAX;
+                if (mine) pair_exact(c + 8 * j, cm[j], wr[j], dr, be, bk);
+                resolve(4 * ch + j, be, bk);
+              }
+            }
+          };
+          uint32_t ra[32], rb[32];
+          if (ok) load(0, ra);
+#pragma unroll
+          for (int ch = 0; ch < Cf::NCH; ch += 2) {
+            if (ok) {
+              ptx::tmem_wait(ra);
+              load(ch + 1, rb);
+            }
+            if (ok) chunk(ch, ra);
+            if (ok) {
+              ptx::tmem_wait(rb);
+              if (ch + 2 < Cf::NCH) load(ch + 2, ra);
+            }
+            if (ch + 2 >= Cf::NCH) {
+              ptx::tc_fence_before();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
+            }
+            if (ok) chunk(ch + 1, rb);
+          }
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(rec_empty);
+        } else {
+          // B = 16: 16-column chunks = 2 ranges, the two K-half accumulators
+          // added as exact integers
+          auto chunk = [&](int ch, const uint32_t* rg) {
+            float c[CW];
 #pragma unroll
             for (int j = 0; j < CW; j += 2) {
               const float2 s2 =
@@ -576,70 +627,27 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
               c[j] = s2.x;
               c[j + 1] = s2.y;
             }
-          }
-          float cm[RPC];
-          uint32_t fl = 0;
-#pragma unroll
-          for (int j = 0; j < RPC; ++j) fl |= screen(c + 8 * j, ch * RPC + j, cm[j]) << j;
-          if (!dvalid) fl = 0;
-          if (__any_sync(0xffffffffu, fl != 0)) slow(c, cm, ch, fl);
-        };
-
-        if constexpr (Cf::NKC == 1) {
-          // the whole 128-column tile into registers, then the accumulator
-          // goes back to the MMA before any scoring
-          uint32_t r0[32], r1[32], r2[32], r3[32];
-          if (ok) {
-            load(0, r0);
-            load(1, r1);
-            load(2, r2);
-            load(3, r3);
-            ptx::tmem_wait(r0);
-            ptx::tmem_dep(r1);
-            ptx::tmem_dep(r2);
-            ptx::tmem_dep(r3);
-          }
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
-          if (ok) {
-            // screen all 16 ranges of the tile (independent chains, no
-            // branch), then one vote before any exact work
-            float cm[kTileRanges];
+            float cm[RPC];
             uint32_t fl = 0;
-            auto screen4 = [&](const uint32_t* rg, int ch) {
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                float v[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(rg[8 * j + k]);
-                fl |= screen(v, ch * 4 + j, cm[ch * 4 + j]) << (ch * 4 + j);
-              }
-            };
-            screen4(r0, 0);
-            screen4(r1, 1);
-            screen4(r2, 2);
-            screen4(r3, 3);
+            for (int j = 0; j < RPC; ++j) {
+              const int r = ch * RPC + j;
+              fl |= screen(c + 8 * j, w[r], thr[r], cm[j]) << j;
+            }
             if (!dvalid) fl = 0;
             if (__any_sync(0xffffffffu, fl != 0)) {
-              auto slow4 = [&](const uint32_t* rg, int ch) {
-                const uint32_t f4 = (fl >> (4 * ch)) & 0xFu;
-                if (__any_sync(0xffffffffu, f4 != 0)) {
-                  float c[32];
+              const DomRec dr = sDom[dl];
 #pragma unroll
-                  for (int j = 0; j < 32; ++j) c[j] = __uint_as_float(rg[j]);
-                  slow(c, cm + 4 * ch, ch, f4);
-                }
-              };
-              slow4(r0, 0);
-              slow4(r1, 1);
-              slow4(r2, 2);
-              slow4(r3, 3);
+              for (int j = 0; j < RPC; ++j) {
+                const int r = ch * RPC + j;
+                const bool mine = (fl >> j) & 1u;
+                if (!__any_sync(0xffffffffu, mine)) continue;
+                int64_t be = INT64_MAX, bk = INT64_MAX;
+                if (mine) pair_exact(c + 8 * j, cm[j], w[r], dr, be, bk);
+                thr[r] = fminf(thr[r], resolve(r, be, bk));
+              }
             }
-          }
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(rec_empty);
-        } else {
+          };
           if (ok) {
             // two TMEM loads in flight: the next chunk's with this chunk's work
             uint32_t ra[32], rb[32];

@@ -220,20 +220,28 @@ __global__ void k_sel_bases(SelState* st, int n_images) {
 }
 
 // The same selection and the stable compaction of the kept positions in one
-// block per image, for pools of at most kSelFusedMax positions: the five
-// digit passes run over the image's keys from L2 with the histogram in
-// shared memory, then each thread compacts a contiguous run of positions.
+// block per image, for pools of at most kSelFusedMax positions.  The first
+// two digit passes read the image's keys from L2 (histograms in shared
+// memory); the second also gathers the keys that still share the prefix, so
+// the last three passes usually run on shared memory alone.  The compaction
+// then gives each warp a contiguous run of positions: a counting sweep, a
+// scan of the 32 warp totals, and an ordered write with ballot ranks.
 constexpr int kSelFusedThreads = 1024;
 constexpr int64_t kSelFusedMax = (int64_t)1 << 20;
+constexpr int kSelCand = 4096;
 
 __global__ void __launch_bounds__(kSelFusedThreads)
 k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ off,
                  const int64_t* __restrict__ slot_off, double pct, SelState* __restrict__ st,
                  int32_t* __restrict__ kept, unsigned int* __restrict__ umax) {
   __shared__ uint32_t hist[kSelBins];
+  __shared__ int64_t cand[kSelCand];
+  __shared__ int n_cand;
   __shared__ int sw[32];
+  __shared__ int wtot[32];
   __shared__ SelState s_st;
   const int im = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t o0 = off[im], P = off[im + 1] - o0;
   const int64_t* k = keys + o0;
   if (threadIdx.x == 0) {
@@ -243,8 +251,10 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
     SelState z{};
     z.rank = (P > 0) ? (P - 1 - ih) : 0;
     s_st = z;
+    n_cand = 0;
     if (im == 0) *umax = 0;  // the packer's running maximum starts here
   }
+  bool in_smem = false;
   for (int pass = 0; pass < kSelPasses; ++pass) {
     const int shift = (kSelPasses - 1 - pass) * kSelBits;
     for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) hist[i] = 0;
@@ -252,10 +262,33 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
     // every thread reads the state before the one that owns the digit
     // rewrites it below
     const int64_t prefix = s_st.prefix, rank = s_st.rank;
-#pragma unroll 4
-    for (int64_t g = threadIdx.x; g < P; g += blockDim.x) {
-      const int64_t kk = k[g];
-      if ((kk >> (shift + kSelBits)) == prefix) atomicAdd(&hist[(kk >> shift) & (kSelBins - 1)], 1u);
+    if (in_smem) {
+      const int nc = n_cand;
+      for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+        const int64_t kk = cand[i];
+        if ((kk >> (shift + kSelBits)) == prefix) atomicAdd(&hist[(kk >> shift) & (kSelBins - 1)], 1u);
+      }
+    } else {
+      // eight independent loads in flight per thread before any atomics
+      constexpr int U = 8;
+      for (int64_t g0 = threadIdx.x; g0 < P; g0 += (int64_t)U * blockDim.x) {
+        int64_t kk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t g = g0 + (int64_t)u * blockDim.x;
+          kk[u] = g < P ? __ldg(k + g) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (kk[u] >= 0 && (kk[u] >> (shift + kSelBits)) == prefix) {
+            atomicAdd(&hist[(kk[u] >> shift) & (kSelBins - 1)], 1u);
+            if (pass == 1) {
+              const int i = atomicAdd(&n_cand, 1);
+              if (i < kSelCand) cand[i] = kk[u];
+            }
+          }
+        }
+      }
     }
     __syncthreads();
     const int c = threadIdx.x < kSelBins ? (int)hist[threadIdx.x] : 0;
@@ -275,19 +308,46 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
       s_st = x;
     }
     __syncthreads();
+    if (pass == 1) in_smem = n_cand <= kSelCand;  // uniform: read after the barrier
   }
   // stable compaction: kept = key below the threshold (or equal, fallback)
   const int64_t thr = s_st.thr;
   const bool fb = s_st.fallback != 0;
-  const int64_t chunk = ceil_div64(P, blockDim.x);
-  const int64_t g0 = (int64_t)threadIdx.x * chunk, g1 = min(P, g0 + chunk);
+  const int64_t seg = ceil_div64(ceil_div64(P, 32), 32) * 32;  // per warp, a multiple of 32
+  const int64_t g0 = (int64_t)warp * seg, g1 = min(P, g0 + seg);
   int cnt = 0;
-  for (int64_t g = g0; g < g1; ++g) cnt += fb ? (k[g] <= thr) : (k[g] < thr);
-  int tot;
-  int r = block_excl_scan(cnt, sw, &tot);
+  for (int64_t gb = g0; gb < g1; gb += 8 * 32) {
+    int64_t kk[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t g = gb + u * 32 + lane;
+      kk[u] = g < g1 ? __ldg(k + g) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) cnt += kk[u] >= 0 && (fb ? (kk[u] <= thr) : (kk[u] < thr));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) wtot[warp] = cnt;
+  __syncthreads();
+  int base = 0;
+  for (int w2 = 0; w2 < warp; ++w2) base += wtot[w2];
   int32_t* out = kept + slot_off[im];
-  for (int64_t g = g0; g < g1; ++g)
-    if (fb ? (k[g] <= thr) : (k[g] < thr)) out[r++] = (int32_t)g;
+  for (int64_t gb = g0; gb < g1; gb += 8 * 32) {
+    int64_t kk[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t g = gb + u * 32 + lane;
+      kk[u] = g < g1 ? __ldg(k + g) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const bool f = kk[u] >= 0 && (fb ? (kk[u] <= thr) : (kk[u] < thr));
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (f) out[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)(gb + u * 32 + lane);
+      base += __popc(bal);
+    }
+  }
   if (threadIdx.x == 0) st[im] = s_st;
 }
 
