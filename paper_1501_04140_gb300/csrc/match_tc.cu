@@ -361,12 +361,10 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
     // any CTA has published) in shared memory; the warps share their
     // threshold improvements there (a plain store of a smaller value: a lost
     // race only leaves a looser, still valid, threshold) and publish them to
-    // the other CTAs with atomicMin.  At B <= 8 the warps read w and the
-    // thresholds from shared memory for every chunk; at B = 16 they keep
-    // register copies.
+    // the other CTAs with atomicMin.  The warps read w and the thresholds
+    // from shared memory for every chunk.
     constexpr int RPC = Cf::RPC;
     constexpr int REFRESH = 4;               // tiles between reads of the global thresholds
-    constexpr int RW = Cf::UNI ? 1 : kTileRanges;
     const int ew = warp - kCtlWarps;
     const int h = ew >> 2;
     const int qd = warp & 3;
@@ -414,16 +412,6 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       ptx::named_bar_sync(1, epi_threads);
       if (lane < kTileRanges) mybest[lane] = Cand{INT64_MAX, INT64_MAX};
       __syncwarp();
-      float w[RW], thr[RW];
-      if constexpr (!Cf::UNI) {
-#pragma unroll
-        for (int r = 0; r < kTileRanges; r += 4) {
-          const float4 wv = *(const float4*)(sW + r);
-          const float4 tv = *(const float4*)(sThr + r);
-          w[r] = wv.x, w[r + 1] = wv.y, w[r + 2] = wv.z, w[r + 3] = wv.w;
-          thr[r] = tv.x, thr[r + 1] = tv.y, thr[r + 2] = tv.z, thr[r + 3] = tv.w;
-        }
-      }
       uint32_t gpre = rv ? __ldcg(a.gthr + g.r0 + rl) : kThrInit;
       int nmine = 0;
 
@@ -452,16 +440,6 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
             if (tg < sThr[lane]) sThr[lane] = tg;
           }
           gpre = rv ? __ldcg(a.gthr + g.r0 + rl) : kThrInit;
-        }
-        if constexpr (!Cf::UNI) {
-#pragma unroll
-          for (int r = 0; r < kTileRanges; r += 4) {
-            const float4 tv = *(const float4*)(sThr + r);
-            thr[r] = fminf(thr[r], tv.x);
-            thr[r + 1] = fminf(thr[r + 1], tv.y);
-            thr[r + 2] = fminf(thr[r + 2], tv.z);
-            thr[r + 3] = fminf(thr[r + 3], tv.w);
-          }
         }
         const uint8_t* sD = Cf::UNI ? sB + db * Cf::ST_BYTES + Cf::OP_BYTES
                                     : smem + Cf::OFF_D + db * Cf::D_BYTES;
@@ -563,62 +541,31 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           return to;
         };
 
-        if constexpr (Cf::UNI) {
-          // 32-column chunks = 4 ranges, two TMEM loads in flight; the
-          // accumulator goes back to the MMA once the last chunk is in
-          // registers
-          auto chunk = [&](int ch, const uint32_t* rg) {
-            const float4 wv4 = *(const float4*)(sW + 4 * ch);
-            const float4 tv4 = *(const float4*)(sThr + 4 * ch);
-            const float wr[4] = {wv4.x, wv4.y, wv4.z, wv4.w};
-            const float tr[4] = {tv4.x, tv4.y, tv4.z, tv4.w};
-            float c[32];
+        // one chunk of CW columns = RPC ranges: the float screen (hot), and
+        // for the rare chunk where some lane passes it, the exact pass on a
+        // local copy in a rolled loop, which keeps the kernel's code small
+        auto slow = [&](const float* c, const float* cm, const float* wr, int ch, uint32_t fl) {
+          float cl[CW], cml[RPC], wl[RPC];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) c[j] = __uint_as_float(rg[j]);
-            float cm[4];
-            uint32_t fl = 0;
+          for (int j = 0; j < CW; ++j) cl[j] = c[j];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) fl |= screen(c + 8 * j, wr[j], tr[j], cm[j]) << j;
-            if (!dvalid) fl = 0;
-            if (__any_sync(0xffffffffu, fl != 0)) {
-              const DomRec dr = sDom[dl];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                const bool mine = (fl >> j) & 1u;
-                if (!__any_sync(0xffffffffu, mine)) continue;
-                int64_t be = INT64_MAX, bk = INT64_MAX;
-                if (mine) pair_exact(c + 8 * j, cm[j], wr[j], dr, be, bk);
-                resolve(4 * ch + j, be, bk);
-              }
-            }
-          };
-          uint32_t ra[32], rb[32];
-          if (ok) load(0, ra);
-#pragma unroll
-          for (int ch = 0; ch < Cf::NCH; ch += 2) {
-            if (ok) {
-              ptx::tmem_wait(ra);
-              load(ch + 1, rb);
-            }
-            if (ok) chunk(ch, ra);
-            if (ok) {
-              ptx::tmem_wait(rb);
-              if (ch + 2 < Cf::NCH) load(ch + 2, ra);
-            }
-            if (ch + 2 >= Cf::NCH) {
-              ptx::tc_fence_before();
-              __syncwarp();
-              if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
-            }
-            if (ok) chunk(ch + 1, rb);
+          for (int j = 0; j < RPC; ++j) cml[j] = cm[j], wl[j] = wr[j];
+          const DomRec dr = sDom[dl];
+#pragma unroll 1
+          for (int j = 0; j < RPC; ++j) {
+            const bool mine = (fl >> j) & 1u;
+            if (!__any_sync(0xffffffffu, mine)) continue;
+            int64_t be = INT64_MAX, bk = INT64_MAX;
+            if (mine) pair_exact(cl + 8 * j, cml[j], wl[j], dr, be, bk);
+            resolve(ch * RPC + j, be, bk);
           }
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(rec_empty);
-        } else {
-          // B = 16: 16-column chunks = 2 ranges, the two K-half accumulators
-          // added as exact integers
-          auto chunk = [&](int ch, const uint32_t* rg) {
-            float c[CW];
+        };
+        auto chunk = [&](int ch, const uint32_t* rg) {
+          float c[CW];
+          if constexpr (Cf::NKC == 1) {
+#pragma unroll
+            for (int j = 0; j < CW; ++j) c[j] = __uint_as_float(rg[j]);
+          } else {  // B = 16: the two K-half accumulators, added as exact integers
 #pragma unroll
             for (int j = 0; j < CW; j += 2) {
               const float2 s2 =
@@ -627,48 +574,49 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
               c[j] = s2.x;
               c[j + 1] = s2.y;
             }
-            float cm[RPC];
-            uint32_t fl = 0;
+          }
+          float wr[RPC], tr[RPC];
+          if constexpr (RPC == 4) {
+            const float4 wv4 = *(const float4*)(sW + 4 * ch);
+            const float4 tv4 = *(const float4*)(sThr + 4 * ch);
+            wr[0] = wv4.x, wr[1] = wv4.y, wr[2] = wv4.z, wr[3] = wv4.w;
+            tr[0] = tv4.x, tr[1] = tv4.y, tr[2] = tv4.z, tr[3] = tv4.w;
+          } else {
+            const float2 wv2 = *(const float2*)(sW + 2 * ch);
+            const float2 tv2 = *(const float2*)(sThr + 2 * ch);
+            wr[0] = wv2.x, wr[1] = wv2.y;
+            tr[0] = tv2.x, tr[1] = tv2.y;
+          }
+          float cm[RPC];
+          uint32_t fl = 0;
 #pragma unroll
-            for (int j = 0; j < RPC; ++j) {
-              const int r = ch * RPC + j;
-              fl |= screen(c + 8 * j, w[r], thr[r], cm[j]) << j;
-            }
-            if (!dvalid) fl = 0;
-            if (__any_sync(0xffffffffu, fl != 0)) {
-              const DomRec dr = sDom[dl];
-#pragma unroll
-              for (int j = 0; j < RPC; ++j) {
-                const int r = ch * RPC + j;
-                const bool mine = (fl >> j) & 1u;
-                if (!__any_sync(0xffffffffu, mine)) continue;
-                int64_t be = INT64_MAX, bk = INT64_MAX;
-                if (mine) pair_exact(c + 8 * j, cm[j], w[r], dr, be, bk);
-                thr[r] = fminf(thr[r], resolve(r, be, bk));
-              }
-            }
-          };
+          for (int j = 0; j < RPC; ++j) fl |= screen(c + 8 * j, wr[j], tr[j], cm[j]) << j;
+          if (!dvalid) fl = 0;
+          if (__any_sync(0xffffffffu, fl != 0)) slow(c, cm, wr, ch, fl);
+        };
+
+        // two TMEM loads in flight; the accumulator goes back to the MMA
+        // once the tile's last chunk is in registers
+        uint32_t ra[32], rb[32];
+        if (ok) load(0, ra);
+#pragma unroll 1
+        for (int ch = 0; ch < Cf::NCH; ch += 2) {
           if (ok) {
-            // two TMEM loads in flight: the next chunk's with this chunk's work
-            uint32_t ra[32], rb[32];
-            load(0, ra);
-#pragma unroll
-            for (int ch = 0; ch < Cf::NCH; ch += 2) {
-              ptx::tmem_wait(ra);
-              load(ch + 1, rb);
-              chunk(ch, ra);
-              ptx::tmem_wait(rb);
-              if (ch + 2 < Cf::NCH) load(ch + 2, ra);
-              chunk(ch + 1, rb);
-            }
+            ptx::tmem_wait(ra);
+            load(ch + 1, rb);
+            chunk(ch, ra);
+            ptx::tmem_wait(rb);
+            if (ch + 2 < Cf::NCH) load(ch + 2, ra);
           }
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) {
-            ptx::mbar_arrive(&acc_empty[ab]);
-            ptx::mbar_arrive(rec_empty);
+          if (ch + 2 >= Cf::NCH) {
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
           }
+          if (ok) chunk(ch + 1, rb);
         }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(rec_empty);
       }
       // merge the warps' bests per range; one thread per range writes the
       // item's partial
