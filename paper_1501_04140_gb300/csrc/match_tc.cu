@@ -141,6 +141,7 @@ constexpr int MODE_M1 = 0, MODE_M2 = 1, MODE_GRID = 2;
 
 struct ItemGeo {
   int im, nr, t0, t1, nkept;
+  int rot;       // the item's tiles run from t0 + rot, wrapping at t1
   int64_t r0, slot0;
   int64_t pidx;  // index of the item's partials: (range tile) * chunks + chunk
 };
@@ -163,8 +164,17 @@ __device__ inline ItemGeo item_geo(const MatchArgs& a, int64_t it, int CH) {
   const int nt = ceil_div(g.nkept, kTileDoms);
   g.t0 = c * CH;
   g.t1 = min(nt, g.t0 + CH);
+  // concurrent items of one chunk start at different tiles, so the CTAs
+  // do not all fetch the same tile block from L2 at the same moment
+  g.rot = g.t1 > g.t0 ? (int)((mt * 53) % (g.t1 - g.t0)) : 0;
   g.slot0 = a.pool_off[g.im];
   return g;
+}
+
+// Tile k (0-based) of an item in its rotated order.
+__device__ inline int item_tile(const ItemGeo& g, int k) {
+  const int t = g.t0 + g.rot + k;
+  return t < g.t1 ? t : t - (g.t1 - g.t0);
 }
 
 // Skip a candidate whose float score is above this: an upper bound of the
@@ -257,7 +267,8 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
         ptx::bulk_g2s(sA + ab * Cf::A_BYTES, a.apack + g.r0 * 8 * Cf::Kp, Cf::A_BYTES,
                       &a_full[ab]);
         ++ai;
-        for (int t = g.t0; ok && t < g.t1; ++t) {
+        for (int kt = 0; ok && kt < g.t1 - g.t0; ++kt) {
+          const int t = item_tile(g, kt);
           const int64_t tile_g = g.slot0 / kTileDoms + t;
           if constexpr (!Cf::UNI) {
             // the tile's scoring records: a ring of their own, ND tiles ahead
@@ -312,7 +323,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           break;
         }
         const uint8_t* sR = sA + rb * Cf::A_BYTES;
-        for (int t = g.t0; ok && t < g.t1; ++t) {
+        for (int kt = 0; ok && kt < g.t1 - g.t0; ++kt) {
           const int ab = ti % Cf::NACC;
           if (!ptx::mbar_wait(&acc_empty[ab], ((ti / Cf::NACC) & 1) ^ 1) || *abort_flag) {
             ok = false;
@@ -415,8 +426,9 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       uint32_t gpre = rv ? __ldcg(a.gthr + g.r0 + rl) : kThrInit;
       int nmine = 0;
 
-      for (int t = g.t0; t < g.t1; ++t, ++ti) {
+      for (int kt = 0; kt < g.t1 - g.t0; ++kt, ++ti) {
         if ((int)(ti % EG) != h) continue;
+        const int t = item_tile(g, kt);
         const int ab = ti % Cf::NACC;
         // the tile's scoring records: in its whole-tile stage (B <= 8; one
         // stage per tile, so stage fill = tile), or in the record ring
@@ -465,11 +477,10 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
         // float screen of one (domain, range) pair: the maximum of the range's
         // 8 isometry correlations, then the best score over S against the
         // range's threshold
-        auto screen = [&](const float* v, float wr, float tr, float& cmax) -> uint32_t {
+        auto screen = [&](const float* v, float wr, float tr, float& cmax, float& sc) -> uint32_t {
           cmax = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
                        ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
           const float y = fmaf(nX, wr, cmax);
-          float sc;
           if constexpr (MODE == MODE_GRID) {
             float p = rintf(y * F1);
             p = fminf(fmaxf(p, 0.f), qf);
@@ -510,24 +521,12 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           }
         };
 
-        // the warp's lexicographic minimum of range r's flagged pairs, then
-        // this warp's best of r and the shared thresholds; returns the new
-        // threshold (+inf if nothing improved)
-        auto resolve = [&](int r, int64_t be, int64_t bk) -> float {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const int64_t e2 = __shfl_xor_sync(0xffffffffu, be, o);
-            const int64_t k2 = __shfl_xor_sync(0xffffffffu, bk, o);
-            if (e2 < be || (e2 == be && k2 < bk)) {
-              be = e2;
-              bk = k2;
-            }
-          }
-          // every lane holds the warp's best of this range now
+        // this warp's best of range r and the shared thresholds, from the
+        // warp's best candidate (held by every lane)
+        auto resolve = [&](int r, int64_t be, int64_t bk) {
           const Cand cur = mybest[r];
-          float to = INFINITY;
           if (be < cur.score || (be == cur.score && bk < cur.key)) {
-            to = thr_of(be, inv_up, inv_dn, sDelta[r]);
+            const float to = thr_of(be, inv_up, inv_dn, sDelta[r]);
             __syncwarp();
             if (lane == 0) {
               mybest[r] = Cand{be, bk};
@@ -538,26 +537,53 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
             }
             __syncwarp();
           }
-          return to;
         };
 
         // one chunk of CW columns = RPC ranges: the float screen (hot), and
         // for the rare chunk where some lane passes it, the exact pass on a
         // local copy in a rolled loop, which keeps the kernel's code small
-        auto slow = [&](const float* c, const float* cm, const float* wr, int ch, uint32_t fl) {
-          float cl[CW], cml[RPC], wl[RPC];
+        //
+        // Of the flagged lanes only those whose float score lies within two
+        // margins of the warp's smallest can hold the exact winner (each
+        // score is within a quarter margin of its exact value, and the
+        // smallest one's pair is scored exactly); usually that is one lane,
+        // which scores its pair and broadcasts it.
+        auto slow = [&](const float* c, const float* cm, const float* scs, const float* wr, int ch,
+                        uint32_t fl) {
+          float cl[CW], cml[RPC], sl[RPC], wl[RPC];
 #pragma unroll
           for (int j = 0; j < CW; ++j) cl[j] = c[j];
 #pragma unroll
-          for (int j = 0; j < RPC; ++j) cml[j] = cm[j], wl[j] = wr[j];
-          const DomRec dr = sDom[dl];
+          for (int j = 0; j < RPC; ++j) cml[j] = cm[j], sl[j] = scs[j], wl[j] = wr[j];
 #pragma unroll 1
           for (int j = 0; j < RPC; ++j) {
             const bool mine = (fl >> j) & 1u;
             if (!__any_sync(0xffffffffu, mine)) continue;
+            const int r = ch * RPC + j;
+            float mn = mine ? sl[j] : INFINITY;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            const float lim = __fadd_ru(mn, 2.0f * sDelta[r]);
+            const bool need = mine && sl[j] <= lim;
+            const unsigned bal = __ballot_sync(0xffffffffu, need);
             int64_t be = INT64_MAX, bk = INT64_MAX;
-            if (mine) pair_exact(cl + 8 * j, cml[j], wl[j], dr, be, bk);
-            resolve(ch * RPC + j, be, bk);
+            if (need) pair_exact(cl + 8 * j, cml[j], wl[j], sDom[dl], be, bk);
+            if (__popc(bal) == 1) {
+              const int src = __ffs(bal) - 1;
+              be = __shfl_sync(0xffffffffu, be, src);
+              bk = __shfl_sync(0xffffffffu, bk, src);
+            } else {
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) {
+                const int64_t e2 = __shfl_xor_sync(0xffffffffu, be, o);
+                const int64_t k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+                if (e2 < be || (e2 == be && k2 < bk)) {
+                  be = e2;
+                  bk = k2;
+                }
+              }
+            }
+            resolve(r, be, bk);
           }
         };
         auto chunk = [&](int ch, const uint32_t* rg) {
@@ -587,12 +613,12 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
             wr[0] = wv2.x, wr[1] = wv2.y;
             tr[0] = tv2.x, tr[1] = tv2.y;
           }
-          float cm[RPC];
+          float cm[RPC], scs[RPC];
           uint32_t fl = 0;
 #pragma unroll
-          for (int j = 0; j < RPC; ++j) fl |= screen(c + 8 * j, wr[j], tr[j], cm[j]) << j;
+          for (int j = 0; j < RPC; ++j) fl |= screen(c + 8 * j, wr[j], tr[j], cm[j], scs[j]) << j;
           if (!dvalid) fl = 0;
-          if (__any_sync(0xffffffffu, fl != 0)) slow(c, cm, wr, ch, fl);
+          if (__any_sync(0xffffffffu, fl != 0)) slow(c, cm, scs, wr, ch, fl);
         };
 
         // two TMEM loads in flight; the accumulator goes back to the MMA
