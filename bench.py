@@ -62,7 +62,7 @@ class Clocks:
         try:
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
@@ -265,9 +265,11 @@ def run_ours(args):
     value = ws * matches / (t_max * 1e-3)
 
     # roofline of the dominant kernel: the tensor matcher at its costliest
-    # level.  Per match (row x kept domain) it does 2n MMA flops (tensor
-    # pipe) and an epilogue of 1 + 2|S| FP32 lane-ops (y, then a score and a
-    # min per s); whichever needs longer at its peak bounds the level.
+    # level.  Per match (range x isometry x kept domain) it does 2n MMA flops
+    # (tensor pipe).  Its epilogue works per (range, domain) pair of 8
+    # matches: 7 two-input maxima over the isometries, then y, one score per
+    # s, |S| - 1 minima and one compare, i.e. (8 + 2|S|) / 8 FP32 lane-ops
+    # per match.  Whichever needs longer at its peak bounds the level.
     hbm, bf16, peak_kind = _peaks()
     props = torch.cuda.get_device_properties(local)
     sm_mhz = _sm_max_mhz()
@@ -279,7 +281,7 @@ def run_ours(args):
         B = s["size"]
         n_s = 1 if B == 16 else 2  # predefined S of Sec. 3.1
         flop = 2.0 * B * B * s["matches"]
-        ops = (1 + 2 * n_s) * s["matches"]
+        ops = (8 + 2 * n_s) / 8.0 * s["matches"]
         sec = lv_ms[l] * 1e-3
         tensor_bound = flop / (bf16 * 1e12) >= ops / (alu_peak * 1e12)
         ach = (flop if tensor_bound else ops) / sec / 1e12 if sec > 0 else 0.0
@@ -368,7 +370,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=16.0,

@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       for (int64_t it = blockIdx.x; ok && it < items; it += gridDim.x) {
         const ItemGeo g = item_geo(a, it, CH);
         const int ab = ai % Cf::NA;
-        if (!ptx::mbar_wait(&a_empty[ab], ((ai / Cf::NA) & 1) ^ 1) || *abort_flag) {
+        if (!ptx::mbar_spin(&a_empty[ab], ((ai / Cf::NA) & 1) ^ 1) || *abort_flag) {
           ok = false;
           break;
         }
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           if constexpr (!Cf::UNI) {
             // the tile's scoring records: a ring of their own, ND tiles ahead
             const int db = di % Cf::ND;
-            if (!ptx::mbar_wait(&d_empty[db], ((di / Cf::ND) & 1) ^ 1) || *abort_flag) {
+            if (!ptx::mbar_spin(&d_empty[db], ((di / Cf::ND) & 1) ^ 1) || *abort_flag) {
               ok = false;
               break;
             }
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           }
           for (int kc = 0; kc < Cf::NKC; ++kc) {
             const int st = si % Cf::NST;
-            if (!ptx::mbar_wait(&empty_b[st], ((si / Cf::NST) & 1) ^ 1) || *abort_flag) {
+            if (!ptx::mbar_spin(&empty_b[st], ((si / Cf::NST) & 1) ^ 1) || *abort_flag) {
               ok = false;
               break;
             }
@@ -302,12 +302,12 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       // drain: every copy this thread issued has landed before the CTA exits
       // (the last fill of each buffer, fill f waits for parity (f / N) & 1)
       for (uint32_t i = 0; i < Cf::NST; ++i)
-        if (si > i) ptx::mbar_wait(&full_b[i], ((i + (si - 1 - i) / Cf::NST * Cf::NST) / Cf::NST) & 1);
+        if (si > i) ptx::mbar_spin(&full_b[i], ((i + (si - 1 - i) / Cf::NST * Cf::NST) / Cf::NST) & 1);
       for (uint32_t i = 0; i < Cf::NA; ++i)
-        if (ai > i) ptx::mbar_wait(&a_full[i], ((i + (ai - 1 - i) / Cf::NA * Cf::NA) / Cf::NA) & 1);
+        if (ai > i) ptx::mbar_spin(&a_full[i], ((i + (ai - 1 - i) / Cf::NA * Cf::NA) / Cf::NA) & 1);
       if constexpr (Cf::ND > 0)
         for (uint32_t i = 0; i < Cf::ND; ++i)
-          if (di > i) ptx::mbar_wait(&d_full[i], ((i + (di - 1 - i) / Cf::ND * Cf::ND) / Cf::ND) & 1);
+          if (di > i) ptx::mbar_spin(&d_full[i], ((i + (di - 1 - i) / Cf::ND * Cf::ND) / Cf::ND) & 1);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -318,20 +318,20 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       for (int64_t it = blockIdx.x; ok && it < items; it += gridDim.x) {
         const ItemGeo g = item_geo(a, it, CH);
         const int rb = ai % Cf::NA;
-        if (!ptx::mbar_wait(&a_full[rb], (ai / Cf::NA) & 1) || *abort_flag) {
+        if (!ptx::mbar_spin(&a_full[rb], (ai / Cf::NA) & 1) || *abort_flag) {
           ok = false;
           break;
         }
         const uint8_t* sR = sA + rb * Cf::A_BYTES;
         for (int kt = 0; ok && kt < g.t1 - g.t0; ++kt) {
           const int ab = ti % Cf::NACC;
-          if (!ptx::mbar_wait(&acc_empty[ab], ((ti / Cf::NACC) & 1) ^ 1) || *abort_flag) {
+          if (!ptx::mbar_spin(&acc_empty[ab], ((ti / Cf::NACC) & 1) ^ 1) || *abort_flag) {
             ok = false;
             break;
           }
           for (int kc = 0; kc < Cf::NKC; ++kc) {
             const int st = si % Cf::NST;
-            if (!ptx::mbar_wait(&full_b[st], (si / Cf::NST) & 1) || *abort_flag) {
+            if (!ptx::mbar_spin(&full_b[st], (si / Cf::NST) & 1) || *abort_flag) {
               ok = false;
               break;
             }
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       }
       if (!ok) fail();
       ptx::mma_commit(done_bar);
-      if (!ptx::mbar_wait(done_bar, 0)) atomicOr(a.status, kStatusTimeout);
+      if (!ptx::mbar_spin(done_bar, 0)) atomicOr(a.status, kStatusTimeout);
     }
   }
   } else {
@@ -426,8 +426,12 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       uint32_t gpre = rv ? __ldcg(a.gthr + g.r0 + rl) : kThrInit;
       int nmine = 0;
 
-      for (int kt = 0; kt < g.t1 - g.t0; ++kt, ++ti) {
-        if ((int)(ti % EG) != h) continue;
+      // this group's tiles of the item: ti = tile counter of the CTA
+      const uint32_t tib = ti;
+      const int len = g.t1 - g.t0;
+      ti += len;
+      for (int kt = (int)((h + EG - tib % EG) % EG); kt < len; kt += EG) {
+        const uint32_t ti = tib + kt;
         const int t = item_tile(g, kt);
         const int ab = ti % Cf::NACC;
         // the tile's scoring records: in its whole-tile stage (B <= 8; one

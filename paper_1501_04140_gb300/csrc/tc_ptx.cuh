@@ -61,6 +61,31 @@ __device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
+// Non-blocking probe of the phase of the given parity.
+__device__ inline bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait by spinning on test_wait (the thread never suspends): for the
+// single-thread producer and MMA issuer, whose wake-up latency sits on the
+// pipeline's critical path.
+__device__ inline bool mbar_spin(uint64_t* bar, uint32_t parity) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_test_wait(bar, parity)) return true;
+    if ((i & 255) == 255 && global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
 // 1-D bulk copy global -> shared through the TMA engine; completes `bytes`
 // of the barrier's transaction count.  Addresses 16-byte aligned, size a
 // multiple of 16.
