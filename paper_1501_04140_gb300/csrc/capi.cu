@@ -64,7 +64,7 @@ struct LevelWs {
   void release_all() {
     DevBuf* all[] = {&pool.off,  &pool.img,   &pool.keys,   &pool.sd,    &pool.sq,     &pool.sel,
                      &pool.hist, &pool.kept,  &pool.bpack,  &pool.b32,   &pool.dom,    &pool.domf,
-                     &pool.scan_scratch, &pool.total, &pool.slot_off, &pool.umax, &img, &rec, &n_act, &act_off,
+                     &pool.scan_scratch, &pool.total, &pool.slot_off, &pool.umax, &pool.run_off, &img, &rec, &n_act, &act_off,
                      &act_cnt,   &mom,        &gthr,        &apack,       &a32,        &res,         &acc,
                      &codes,     &acc_cnt,    &rej_cnt,     &code_off,   &item_off,    &chunks,
                      &meta,      &part,       &scan_scr,    &total};
@@ -84,12 +84,15 @@ void pool_geometry(PoolLevel& pl, const std::vector<fic_image>& ims, int B, int 
   pl.n_images = ni;
   pl.h_off.assign(ni + 1, 0);
   pl.h_slot_off.assign(ni + 1, 0);
+  pl.h_run_off.assign(ni + 1, 0);
   pl.h_img.resize(ni);
   for (int i = 0; i < ni; ++i) {
     const int px = (ims[i].width - 2 * B) / L + 1, py = (ims[i].height - 2 * B) / L + 1;
     const int64_t P = (ims[i].width >= 2 * B && ims[i].height >= 2 * B) ? (int64_t)px * py : 0;
     pl.h_img[i] = ImgDev{nullptr, ims[i].width, ims[i].height, ims[i].pitch, px, py};
     pl.h_off[i + 1] = pl.h_off[i] + P;
+    pl.h_run_off[i + 1] =
+        pl.h_run_off[i] + (P > 0 ? (int64_t)py * pool_runs_per_row(px, B, L) : 0);
     pl.h_slot_off[i + 1] = pl.h_slot_off[i] + ceil_div64(P, kTileDoms) * kTileDoms;
   }
   pl.P_tot = pl.h_off[ni];
@@ -103,6 +106,7 @@ int pool_alloc(PoolLevel& pl) {
   int rc = 0;
   rc |= pl.off.reserve(sizeof(int64_t) * (ni + 1));
   rc |= pl.slot_off.reserve(sizeof(int64_t) * (ni + 1));
+  rc |= pl.run_off.reserve(sizeof(int64_t) * (ni + 1));
   rc |= pl.img.reserve(sizeof(ImgDev) * ni);
   rc |= pl.keys.reserve(sizeof(int64_t) * P);
   rc |= pl.sd.reserve(sizeof(int32_t) * P);
@@ -128,6 +132,8 @@ int pool_upload(PoolLevel& pl, const std::vector<const uint8_t*>& dev_pix, cudaS
                                sizeof(int64_t) * (pl.n_images + 1), cudaMemcpyHostToDevice, st));
   FIC_CUDA_TRY(cudaMemcpyAsync(pl.img.p, pl.h_img.data(), sizeof(ImgDev) * pl.n_images,
                                cudaMemcpyHostToDevice, st));
+  FIC_CUDA_TRY(cudaMemcpyAsync(pl.run_off.p, pl.h_run_off.data(),
+                               sizeof(int64_t) * (pl.n_images + 1), cudaMemcpyHostToDevice, st));
   return FIC_OK;
 }
 
@@ -551,7 +557,7 @@ int fic_create(fic_ctx** out, int device) {
   if (!c) return FIC_ENOMEM;
   c->device = device;
   c->nsm = prop.multiProcessorCount;
-  if (match_tc_prepare() != FIC_OK) {
+  if (match_tc_prepare() != FIC_OK || pool_prepare() != FIC_OK) {
     delete c;
     return FIC_ECUDA;
   }
@@ -682,7 +688,7 @@ void fic_pool_free(fic_pool* p) {
   PoolLevel& pl = p->pl;
   DevBuf* all[] = {&pl.off,  &pl.slot_off, &pl.img, &pl.keys, &pl.sd,   &pl.sq,   &pl.sel,
                    &pl.hist, &pl.kept,     &pl.bpack, &pl.b32, &pl.dom, &pl.domf, &pl.scan_scratch,
-                   &pl.total, &pl.umax};
+                   &pl.total, &pl.umax, &pl.run_off};
   for (DevBuf* b : all) b->release();
   p->staging.buf.release();
   delete p;

@@ -44,14 +44,35 @@ struct PoolLevel {
   std::vector<int64_t> h_off;        // n_images + 1 position offsets
   std::vector<int64_t> h_slot_off;   // n_images + 1 slot offsets (multiples of 128)
   std::vector<ImgDev> h_img;         // with px, py of this level
+  std::vector<int64_t> h_run_off;    // n_images + 1: runs of the sliding statistics
   bool want_tc = false, want_f32 = false;
   SSet sset{};
   double pct = 0.5;                  // entropy percentile of the threshold
   int nsm = 0;                       // SMs of the device (grid sizing)
   // per position: off, keys, sd, sq; per slot: slot_off, kept, bpack, b32, dom, domf
   DevBuf off, slot_off, img, keys, sd, sq, sel, hist, kept, bpack, b32, dom, domf, scan_scratch,
-      total, umax;
+      total, umax, run_off;
 };
+
+// Runs of the sliding pool statistics: along a row of pool positions, the
+// positions whose 2x2 cell grid shares a phase (every position for even L,
+// every other one for odd L), kPoolRun at a time.
+constexpr int kPoolRun = 4;
+__host__ __device__ inline int pool_run_step(int L) { return (L & 1) ? 2 : 1; }
+__host__ __device__ inline int pool_run_len(int B, int L) {
+  return pool_run_step(L) * L >= 2 * B ? 1 : kPoolRun;
+}
+// runs of one row of px positions (phase class 0 first)
+__host__ __device__ inline int pool_runs_per_row(int px, int B, int L) {
+  const int st = pool_run_step(L), R = pool_run_len(B, L);
+  int runs = 0;
+  for (int c = 0; c < st; ++c) {
+    const int nc = px > c ? (px - c + st - 1) / st : 0;
+    runs += (nc + R - 1) / R;
+  }
+  return runs;
+}
+int pool_prepare();  // per device, before the first pool build
 
 // Launchers (pool.cu)
 int pool_build(PoolLevel& pl, const int64_t* d_dT, cudaStream_t st);

@@ -128,6 +128,125 @@ k_pool_stats(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off, i
   }
 }
 
+// Sliding version: one lane per run of positions along a row (see
+// pool_run_len), with a lane-private histogram in shared memory (16-bit
+// counts, [grey level][lane], so the lanes of a warp never contend).  The
+// first window of a run is built in full; each next position removes the
+// d = step L pixel columns that leave and adds the d that enter (d / 2 cell
+// columns of 2x2 sums), updating the key by -dT[c] / +dT[c + 1] and the
+// moments by the cells' sums and squares -- the same exact integers as a
+// full recount.
+constexpr int kPoolLaneThreads = 128;
+
+template <int B>
+struct PoolLaneSmem {
+  static constexpr int N4 = 4 * B * B;
+  static constexpr int DT_BYTES = ((N4 + 1) * 8 + 127) / 128 * 128;
+  static constexpr int BYTES = DT_BYTES + (kPoolLaneThreads / 32) * 256 * 32 * 2;
+};
+
+template <int B>
+__global__ void __launch_bounds__(kPoolLaneThreads)
+k_pool_stats_lane(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
+                  const int64_t* __restrict__ run_off, int n_images, int L,
+                  const int64_t* __restrict__ dT_g, int64_t* __restrict__ keys,
+                  int32_t* __restrict__ sd, int32_t* __restrict__ sq) {
+  using Sm = PoolLaneSmem<B>;
+  extern __shared__ __align__(128) uint8_t psm[];
+  int64_t* dT = (int64_t*)psm;
+  const int lane = threadIdx.x & 31;
+  uint16_t* h = (uint16_t*)(psm + Sm::DT_BYTES) + (threadIdx.x >> 5) * (256 * 32) + lane;
+  for (int i = threadIdx.x; i <= Sm::N4; i += blockDim.x) dT[i] = dT_g[i];
+  for (int b = 0; b < 256; ++b) h[b * 32] = 0;
+  __syncthreads();
+  const int step = pool_run_step(L), R = pool_run_len(B, L), d = step * L;
+  const int64_t total = run_off[n_images];
+  for (int64_t gr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gr < total;
+       gr += (int64_t)gridDim.x * blockDim.x) {
+    const int im = find_segment(run_off, n_images, gr);
+    const ImgDev I = imgs[im];
+    const int rpr = pool_runs_per_row(I.px, B, L);
+    const int64_t lr = gr - run_off[im];
+    const int row = (int)(lr / rpr);
+    int rem = (int)(lr % rpr), cls = 0;
+    const int r0 = ((I.px + step - 1) / step + R - 1) / R;  // runs of phase class 0
+    if (rem >= r0) {
+      cls = 1;
+      rem -= r0;
+    }
+    int i = cls + step * rem * R;  // first position of the run (x index)
+    const int y0 = row * L;
+    int x0 = i * L;
+    const uint8_t* base = I.pix + (int64_t)y0 * I.pitch;
+    int64_t key = 0;
+    int s = 0, s2 = 0;
+    auto add = [&](int v) {
+      const int c = h[v * 32] + 1;
+      h[v * 32] = (uint16_t)c;
+      key += dT[c];
+    };
+    auto del = [&](int v) {
+      const int c = h[v * 32];
+      h[v * 32] = (uint16_t)(c - 1);
+      key -= dT[c];
+    };
+    // the run's first window in full
+    for (int ci = 0; ci < B; ++ci) {
+      const uint8_t* p = base + (int64_t)(2 * ci) * I.pitch + x0;
+      for (int cj = 0; cj < B; ++cj) {
+        const int v0 = p[2 * cj], v1 = p[2 * cj + 1], v2 = p[I.pitch + 2 * cj],
+                  v3 = p[I.pitch + 2 * cj + 1];
+        add(v0); add(v1); add(v2); add(v3);
+        const int ds = v0 + v1 + v2 + v3;
+        s += ds;
+        s2 += ds * ds;
+      }
+    }
+    int64_t g = off[im] + (int64_t)row * I.px + i;
+    keys[g] = key;
+    sd[g] = s;
+    sq[g] = s2;
+    for (int m = 1; m < R; ++m) {
+      i += step;
+      if (i >= I.px) break;
+      for (int ci = 0; ci < B; ++ci) {
+        const uint8_t* p = base + (int64_t)(2 * ci) * I.pitch + x0;
+        for (int cc = 0; cc < d; cc += 2) {
+          const int o0 = p[cc], o1 = p[cc + 1], o2 = p[I.pitch + cc], o3 = p[I.pitch + cc + 1];
+          const int n0 = p[2 * B + cc], n1 = p[2 * B + cc + 1], n2 = p[I.pitch + 2 * B + cc],
+                    n3 = p[I.pitch + 2 * B + cc + 1];
+          del(o0); del(o1); del(o2); del(o3);
+          add(n0); add(n1); add(n2); add(n3);
+          const int dso = o0 + o1 + o2 + o3, dsn = n0 + n1 + n2 + n3;
+          s += dsn - dso;
+          s2 += dsn * dsn - dso * dso;
+        }
+      }
+      x0 += d;
+      g += step;
+      keys[g] = key;
+      sd[g] = s;
+      sq[g] = s2;
+    }
+    for (int b = 0; b < 256; ++b) h[b * 32] = 0;
+  }
+}
+
+template <int B>
+static int prepare_pool_B() {
+  return cudaFuncSetAttribute(k_pool_stats_lane<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              PoolLaneSmem<B>::BYTES) == cudaSuccess
+             ? 0
+             : 1;
+}
+
+// Opt the sliding statistics kernels in to their shared memory (per device).
+int pool_prepare() {
+  return (prepare_pool_B<16>() | prepare_pool_B<8>() | prepare_pool_B<4>() | prepare_pool_B<2>())
+             ? FIC_ECUDA
+             : FIC_OK;
+}
+
 // ---------------------------------------------------------------- exact percentile
 // Sec. 3 keeps domains whose entropy is greater than a threshold; the
 // threshold is the pool's entropy at percentile p: sorted ascending by
@@ -230,6 +349,15 @@ constexpr int kSelFusedThreads = 1024;
 constexpr int64_t kSelFusedMax = (int64_t)1 << 20;
 constexpr int kSelCand = 4096;
 
+// Histogram increment combined across the warp: the entropy keys of a pool
+// crowd into few digit values, so the lanes that share a bin add once.
+__device__ inline void hist_add_warp(uint32_t* hist, bool take, int bin) {
+  const unsigned act = __ballot_sync(0xffffffffu, take);
+  if (!take) return;
+  const unsigned same = __match_any_sync(act, bin);
+  if ((threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
+}
+
 __global__ void __launch_bounds__(kSelFusedThreads)
 k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ off,
                  const int64_t* __restrict__ slot_off, double pct, SelState* __restrict__ st,
@@ -264,14 +392,17 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
     const int64_t prefix = s_st.prefix, rank = s_st.rank;
     if (in_smem) {
       const int nc = n_cand;
-      for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-        const int64_t kk = cand[i];
-        if ((kk >> (shift + kSelBits)) == prefix) atomicAdd(&hist[(kk >> shift) & (kSelBins - 1)], 1u);
+      for (int i0 = 0; i0 < nc; i0 += blockDim.x) {  // uniform trip count: warp-wide adds
+        const int i = i0 + threadIdx.x;
+        const int64_t kk = i < nc ? cand[i] : -1;
+        hist_add_warp(hist, kk >= 0 && (kk >> (shift + kSelBits)) == prefix,
+                      (int)((kk >> shift) & (kSelBins - 1)));
       }
     } else {
       // eight independent loads in flight per thread before any atomics
       constexpr int U = 8;
-      for (int64_t g0 = threadIdx.x; g0 < P; g0 += (int64_t)U * blockDim.x) {
+      for (int64_t g00 = 0; g00 < P; g00 += (int64_t)U * blockDim.x) {  // uniform trip count
+        const int64_t g0 = g00 + threadIdx.x;
         int64_t kk[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -280,10 +411,15 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          if (kk[u] >= 0 && (kk[u] >> (shift + kSelBits)) == prefix) {
-            atomicAdd(&hist[(kk[u] >> shift) & (kSelBins - 1)], 1u);
-            if (pass == 1) {
-              const int i = atomicAdd(&n_cand, 1);
+          const bool take = kk[u] >= 0 && (kk[u] >> (shift + kSelBits)) == prefix;
+          hist_add_warp(hist, take, (int)((kk[u] >> shift) & (kSelBins - 1)));
+          if (pass == 1) {  // gather the keys that share the prefix
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            int base = 0;
+            if ((threadIdx.x & 31) == 0 && bal) base = atomicAdd(&n_cand, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (take) {
+              const int i = base + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
               if (i < kSelCand) cand[i] = kk[u];
             }
           }
@@ -485,15 +621,14 @@ k_pack_domains(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
 // ---------------------------------------------------------------- driver
 template <int B>
 static int pool_build_B(PoolLevel& pl, const int64_t* d_dT, cudaStream_t st) {
-  using Gm = PoolGeom<B>;
   const int ni = pl.n_images;
-  const int64_t P = pl.P_tot;
   const int nsm = pl.nsm > 0 ? pl.nsm : 148;
-  const int64_t groups = ceil_div64(P > 0 ? P : 1, Gm::GPB);
-  const int grid = (int)(groups < (int64_t)nsm * 16 ? groups : (int64_t)nsm * 16);
-  k_pool_stats<B><<<grid, Gm::threads, 0, st>>>(pl.img.as<ImgDev>(), pl.off.as<int64_t>(), ni,
-                                                pl.L, d_dT, pl.keys.as<int64_t>(),
-                                                pl.sd.as<int32_t>(), pl.sq.as<int32_t>());
+  const int64_t runs = pl.h_run_off[ni];
+  const int64_t blocks = ceil_div64(runs > 0 ? runs : 1, kPoolLaneThreads);
+  const int grid = (int)(blocks < (int64_t)nsm * 3 ? blocks : (int64_t)nsm * 3);
+  k_pool_stats_lane<B><<<grid, kPoolLaneThreads, PoolLaneSmem<B>::BYTES, st>>>(
+      pl.img.as<ImgDev>(), pl.off.as<int64_t>(), pl.run_off.as<int64_t>(), ni, pl.L, d_dT,
+      pl.keys.as<int64_t>(), pl.sd.as<int32_t>(), pl.sq.as<int32_t>());
   return FIC_OK;
 }
 
