@@ -339,30 +339,26 @@ __global__ void k_sel_bases(SelState* st, int n_images) {
 }
 
 // The same selection and the stable compaction of the kept positions in one
-// block per image, for pools of at most kSelFusedMax positions.  The first
-// two digit passes read the image's keys from L2 (histograms in shared
-// memory); the second also gathers the keys that still share the prefix, so
-// the last three passes usually run on shared memory alone.  The compaction
-// then gives each warp a contiguous run of positions: a counting sweep, a
-// scan of the 32 warp totals, and an ordered write with ballot ranks.
+// block per image, for pools of at most kSelFusedMax positions.  Digits are
+// 12 bits wide (4096 shared-memory bins; keys are below 2^45): the entropy
+// keys of a pool crowd into a narrow band, and wide digits spread them so
+// the bins' atomics rarely collide.  Two passes read the keys from L2; the
+// second also gathers the keys that share the top digit, so the last two
+// passes usually run on shared memory alone.  The compaction then gives each
+// warp a contiguous run of positions: a counting sweep, a scan of the 32 warp
+// totals, and an ordered write with ballot ranks.
 constexpr int kSelFusedThreads = 1024;
 constexpr int64_t kSelFusedMax = (int64_t)1 << 20;
-constexpr int kSelCand = 4096;
-
-// Histogram increment combined across the warp: the entropy keys of a pool
-// crowd into few digit values, so the lanes that share a bin add once.
-__device__ inline void hist_add_warp(uint32_t* hist, bool take, int bin) {
-  const unsigned act = __ballot_sync(0xffffffffu, take);
-  if (!take) return;
-  const unsigned same = __match_any_sync(act, bin);
-  if ((threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
-}
+constexpr int kSelCand = 3584;  // keeps the block under 48 KB of static shared memory
+constexpr int kSelWBits = 12;
+constexpr int kSelWBins = 1 << kSelWBits;
+constexpr int kSelWPasses = 4;  // 48 >= 45 key bits
 
 __global__ void __launch_bounds__(kSelFusedThreads)
 k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ off,
                  const int64_t* __restrict__ slot_off, double pct, SelState* __restrict__ st,
                  int32_t* __restrict__ kept, unsigned int* __restrict__ umax) {
-  __shared__ uint32_t hist[kSelBins];
+  __shared__ uint32_t hist[kSelWBins];
   __shared__ int64_t cand[kSelCand];
   __shared__ int n_cand;
   __shared__ int sw[32];
@@ -383,26 +379,24 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
     if (im == 0) *umax = 0;  // the packer's running maximum starts here
   }
   bool in_smem = false;
-  for (int pass = 0; pass < kSelPasses; ++pass) {
-    const int shift = (kSelPasses - 1 - pass) * kSelBits;
-    for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) hist[i] = 0;
+  constexpr int BPT = kSelWBins / kSelFusedThreads;  // bins per thread in the scan
+  for (int pass = 0; pass < kSelWPasses; ++pass) {
+    const int shift = (kSelWPasses - 1 - pass) * kSelWBits;
+    for (int i = threadIdx.x; i < kSelWBins; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     // every thread reads the state before the one that owns the digit
     // rewrites it below
     const int64_t prefix = s_st.prefix, rank = s_st.rank;
     if (in_smem) {
       const int nc = n_cand;
-      for (int i0 = 0; i0 < nc; i0 += blockDim.x) {  // uniform trip count: warp-wide adds
-        const int i = i0 + threadIdx.x;
-        const int64_t kk = i < nc ? cand[i] : -1;
-        hist_add_warp(hist, kk >= 0 && (kk >> (shift + kSelBits)) == prefix,
-                      (int)((kk >> shift) & (kSelBins - 1)));
+      for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+        const int64_t kk = cand[i];
+        if ((kk >> (shift + kSelWBits)) == prefix)
+          atomicAdd(&hist[(kk >> shift) & (kSelWBins - 1)], 1u);
       }
     } else {
-      // eight independent loads in flight per thread before any atomics
       constexpr int U = 8;
-      for (int64_t g00 = 0; g00 < P; g00 += (int64_t)U * blockDim.x) {  // uniform trip count
-        const int64_t g0 = g00 + threadIdx.x;
+      for (int64_t g0 = threadIdx.x; g0 < P; g0 += (int64_t)U * blockDim.x) {
         int64_t kk[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -411,15 +405,10 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const bool take = kk[u] >= 0 && (kk[u] >> (shift + kSelBits)) == prefix;
-          hist_add_warp(hist, take, (int)((kk[u] >> shift) & (kSelBins - 1)));
-          if (pass == 1) {  // gather the keys that share the prefix
-            const unsigned bal = __ballot_sync(0xffffffffu, take);
-            int base = 0;
-            if ((threadIdx.x & 31) == 0 && bal) base = atomicAdd(&n_cand, __popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (take) {
-              const int i = base + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
+          if (kk[u] >= 0 && (kk[u] >> (shift + kSelWBits)) == prefix) {
+            atomicAdd(&hist[(kk[u] >> shift) & (kSelWBins - 1)], 1u);
+            if (pass == 1) {  // gather the keys that share the top digit
+              const int i = atomicAdd(&n_cand, 1);
               if (i < kSelCand) cand[i] = kk[u];
             }
           }
@@ -427,21 +416,34 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
       }
     }
     __syncthreads();
-    const int c = threadIdx.x < kSelBins ? (int)hist[threadIdx.x] : 0;
+    // exclusive scan of the bins: BPT consecutive bins per thread
+    uint32_t c[BPT];
+    int csum = 0;
+#pragma unroll
+    for (int u = 0; u < BPT; ++u) {
+      c[u] = hist[threadIdx.x * BPT + u];
+      csum += (int)c[u];
+    }
     int tot;
-    const int before = block_excl_scan(c, sw, &tot);
-    if (threadIdx.x < kSelBins && tot > 0 && before <= rank && rank < before + c) {
-      SelState x = s_st;
-      x.prefix = (prefix << kSelBits) | threadIdx.x;
-      x.rank = rank - before;
-      x.nlt += before;
-      if (pass == kSelPasses - 1) {
-        x.thr = x.prefix;
-        x.nle = x.nlt + c;
-        x.fallback = (x.nlt == 0) ? 1 : 0;
-        x.nkept = (int32_t)(x.fallback ? x.nle : x.nlt);
+    int before = block_excl_scan(csum, sw, &tot);
+    if (tot > 0 && before <= rank && rank < before + csum) {
+#pragma unroll
+      for (int u = 0; u < BPT; ++u) {
+        if (before <= rank && rank < before + (int)c[u]) {
+          SelState x = s_st;
+          x.prefix = (prefix << kSelWBits) | (threadIdx.x * BPT + u);
+          x.rank = rank - before;
+          x.nlt += before;
+          if (pass == kSelWPasses - 1) {
+            x.thr = x.prefix;
+            x.nle = x.nlt + c[u];
+            x.fallback = (x.nlt == 0) ? 1 : 0;
+            x.nkept = (int32_t)(x.fallback ? x.nle : x.nlt);
+          }
+          s_st = x;
+        }
+        before += (int)c[u];
       }
-      s_st = x;
     }
     __syncthreads();
     if (pass == 1) in_smem = n_cand <= kSelCand;  // uniform: read after the barrier
