@@ -37,6 +37,30 @@ UNIT = "matches/s"
 WORKLOAD = ("512x512 8-bit synthetic (seed 1, one textured quadrant), quadtree 16-8-4-2, "
             "L=2, RMS 8, predefined S, median entropy threshold")
 
+# Other workloads (informational runs, --workload): the uneven-size batch and
+# the 4096 x 4096 image with the full L = 1 pool.
+WORKLOADS = {
+    "512": dict(desc=WORKLOAD, metric=METRIC, step=2),
+    "batch64": dict(desc=("64 8-bit synthetic images of uneven sizes (seeds 1000-1063, sizes from "
+                          "{256x256, 384x512, 512x512, 768x1024, 1024x1024} by a seeded stream, one "
+                          "textured tile each), quadtree 16-8-4-2, L=2, RMS 8, predefined S, median "
+                          "entropy threshold, one launch per level over all images"),
+                    metric="range x domain x isometry matches/s (64-image uneven batch encode)",
+                    step=2),
+    "4096": dict(desc=("4096x4096 8-bit synthetic (seed 1, 8 textured tiles), quadtree 16-8-4-2, "
+                       "L=1 (full pool), RMS 8, predefined S, median entropy threshold"),
+                 metric="range x domain x isometry matches/s (4096x4096 L=1 encode)", step=1),
+}
+
+
+def workload_images(name):
+    from paper_1501_04140_gb300.synth import batch_specs, synth_image
+    if name == "batch64":
+        return [synth_image(W, H, sd, n_textured=1) for (W, H, sd) in batch_specs(64, 1000, 42)]
+    if name == "4096":
+        return [synth_image(4096, 4096, 1, n_textured=8)]
+    return [synth_image(W_IMG, H_IMG, SEED, n_textured=1)]
+
 
 def _peaks():
     try:
@@ -202,18 +226,28 @@ def run_ours(args):
     from paper_1501_04140_gb300.synth import synth_image
     import oracle
 
-    img = synth_image(W_IMG, H_IMG, SEED, n_textured=1)
+    wl = WORKLOADS[args.workload]
+    imgs = workload_images(args.workload)
+    img = imgs[0]
     ctx = fic.Context(local)
     stream = torch.cuda.Stream()
-    d_img = torch.from_numpy(img).cuda()
+    d_imgs = [torch.from_numpy(im).cuda() for im in imgs]
+    d_img = d_imgs if len(d_imgs) > 1 else d_imgs[0]
     l2_flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def time_path(precision, steps, warmup, profile=False):
-        p = fic.default_params(precision=precision)
+        p = fic.default_params(precision=precision, domain_step=wl["step"])
         with torch.cuda.stream(stream):
             code = ctx.encode(d_img, p, stream=stream)
         torch.cuda.synchronize()
-        stats = code.stats(0)
+        # per level, summed over the images
+        per_img = [code.stats(i) for i in range(len(imgs))]
+        stats = []
+        for lv in range(len(per_img[0])):
+            agg = dict(per_img[0][lv])
+            for k in ("n_active", "n_kept", "matches"):
+                agg[k] = sum(ps[lv][k] for ps in per_img)
+            stats.append(agg)
         if profile:
             code.set_profiling(True)
         for _ in range(warmup):
@@ -253,7 +287,7 @@ def run_ours(args):
     ms = statistics.mean(times)
     n_kernels = code.graph_kernels()
     dec = code.decode(0)
-    psnr = oracle.psnr(img, dec)
+    psnr = oracle.psnr(img, dec)  # the first image
 
     # max over ranks
     t_max = ms
@@ -304,57 +338,64 @@ def run_ours(args):
                                 f"FP32 lanes: {props.multi_processor_count} SMs x 128 x "
                                 f"{sm_mhz:.0f} MHz (derived)")}
 
-    # plain FP32 CUDA-core path, same workload
-    code32, stats32, times32, _, _ = time_path(fic.FIC_PREC_FP32, max(3, args.steps // 4), 2)
-    ms32 = statistics.mean(times32)
-    psnr32 = oracle.psnr(img, code32.decode(0))
-    matches32 = sum(s["matches"] for s in stats32)
-    code32.free()
+    # plain FP32 CUDA-core path, same workload (not on the 4096 x 4096 run,
+    # where one FP32 encode takes minutes)
+    fp32 = None
+    if args.workload != "4096":
+        code32, stats32, times32, _, _ = time_path(fic.FIC_PREC_FP32, max(3, args.steps // 4), 3)
+        ms32 = statistics.mean(times32)
+        psnr32 = oracle.psnr(img, code32.decode(0))
+        matches32 = sum(s["matches"] for s in stats32)
+        code32.free()
+        fp32 = {"value": matches32 / (ms32 * 1e-3), "unit": UNIT, "encode_ms": ms32,
+                "psnr_db": psnr32,
+                "speedup_tensor_vs_fp32": (matches / (t_max * 1e-3)) / (matches32 / (ms32 * 1e-3))}
 
-    # end to end through the C ABI with host buffers: pinned host image in,
+    # end to end through the C ABI with host buffers: pinned host images in,
     # every saved map out, both copies inside the timed region
-    pinned = torch.from_numpy(img).pin_memory()
-    p = fic.default_params()
-    code_h = ctx.encode(pinned, p, stream=stream)
+    pinned = [torch.from_numpy(im).pin_memory() for im in imgs]
+    ph = pinned if len(pinned) > 1 else pinned[0]
+    p = fic.default_params(domain_step=wl["step"])
+    code_h = ctx.encode(ph, p, stream=stream)
     torch.cuda.synchronize()
-    n_codes = code_h.count(0)
+    n_codes = sum(code_h.count(i) for i in range(len(imgs)))
     e2e = []
-    for s in range(args.warmup + args.steps):
+    e2e_steps = args.steps if args.workload == "512" else 1
+    e2e_warm = args.warmup if args.workload == "512" else 1
+    for s in range(e2e_warm + e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.encode_again(code_h, pinned, p, stream=stream)
-        out = code_h.transforms(0)
+        ctx.encode_again(code_h, ph, p, stream=stream)
+        outs = [code_h.transforms(i) for i in range(len(imgs))]
         t1 = time.perf_counter()
-        if s >= args.warmup:
+        if s >= e2e_warm:
             e2e.append(t1 - t0)
     e2e_v = ws * matches / statistics.mean(e2e)
-    d2h = len(out) * out.dtype.itemsize + 4 * 8 * 2
+    d2h = sum(len(o) * o.dtype.itemsize for o in outs) + 4 * 8 * 2 * len(imgs)
     code_h.free()
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "512":
         cores = os.cpu_count() or 1
         v, sample = oracle_rate(img, stats, args.cpu_budget, cores)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": wl["metric"], "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16 MMA on exact integers, int64 scoring",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": f"replicas x{ws}",
+            "config": {"workload": wl["desc"], "parallelism": f"replicas x{ws}",
                        "l2": "flushed between steps (256 MB write)",
                        "encode_ms": t_max, "psnr_db": psnr, "n_codes": n_codes,
-                       "matches_per_step": matches},
-            "fp32_path": {"value": matches32 / (ms32 * 1e-3), "unit": UNIT, "encode_ms": ms32,
-                          "psnr_db": psnr32,
-                          "speedup_tensor_vs_fp32": (matches / (t_max * 1e-3)) /
-                                                    (matches32 / (ms32 * 1e-3))},
+                       "n_images": len(imgs), "matches_per_step": matches},
+            "fp32_path": fp32,
             "levels": levels,
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": W_IMG * H_IMG,
+            "e2e": {"value": e2e_v, "unit": UNIT,
+                    "h2d_bytes_per_step": sum(im.size for im in imgs),
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": n_kernels * args.steps,
             "clocks": clocks,
@@ -377,6 +418,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=16.0,
                     help="seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="512",
+                    help="512 (the headline), batch64 or 4096 (informational runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

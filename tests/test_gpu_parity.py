@@ -353,3 +353,22 @@ def test_graph_replay_and_profiling():
         assert len(prof) == 4 and all(m > 0 and lv >= m for m, lv in prof), prof
     assert code.graph_kernels() > 20
     code.free()
+
+
+def test_pool_parity_large_multi_kernel_select():
+    """A pool above 2^20 positions (1104 x 1104, L = 1, B = 2: 1,212,201
+    positions) takes the multi-kernel radix select; keys, threshold and the
+    kept list match the oracle bit-exactly, for two percentiles."""
+    fic = _fic()
+    ctx = G.ctx()
+    img = synth_image(1104, 1104, 77, n_textured=2)
+    for B, pct in ((2, 0.5), (4, 0.75)):
+        p = fic.default_params(domain_step=1, entropy_percentile=pct)
+        pool = ctx.build_domain_pool(G.dev(img), B, p)
+        info = pool.info()
+        keys_o, kept_o, thr_o, fb_o = oracle.pool_filter(img, B, 1, pct)
+        assert info["pool_size"] == len(keys_o) > (1 << 20)
+        np.testing.assert_array_equal(pool.copy(fic.FIC_POOL_KEYS), keys_o)
+        assert info["thr_key"] == thr_o and info["fallback"] == fb_o
+        np.testing.assert_array_equal(pool.copy(fic.FIC_POOL_KEPT), kept_o)
+        pool.free()
