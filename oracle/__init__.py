@@ -45,7 +45,7 @@ class Params(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("range_size0", C.c_int), ("domain_step", C.c_int),
                 ("rms_threshold", C.c_double), ("single_level", C.c_int), ("s_mode", C.c_int),
                 ("grid_samples", C.c_int), ("entropy_percentile", C.c_double),
-                ("n_threads", C.c_int)]
+                ("n_threads", C.c_int), ("pool_size", C.c_int)]
 
 
 class Code(C.Structure):
@@ -93,7 +93,7 @@ def lib():
             L.oracle_pool_size.argtypes = [C.c_int] * 4 + [_P, _P]
             L.oracle_pool_filter.restype = C.c_int
             L.oracle_pool_filter.argtypes = [_P, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int,
-                                             C.c_double, _P, _P, _P, _P]
+                                             C.c_double, C.c_int, _P, _P, _P, _P]
             L.oracle_decimate.restype = None
             L.oracle_decimate.argtypes = [_P, C.c_long, C.c_int, C.c_int, C.c_int, _P]
             L.oracle_isometry.restype = None
@@ -148,8 +148,10 @@ def pool_size(W, H, B, L):
     return P, nx.value, ny.value
 
 
-def pool_filter(img, B, L, percentile):
-    """Returns (keys[P], kept[n_kept], thr_key, fallback)."""
+def pool_filter(img, B, L, percentile, top_k=0):
+    """Returns (keys[P], kept[n_kept], thr_key, fallback); top_k K > 0 keeps
+    the K highest entropies (Tables 1-2's pool size) instead of the
+    percentile."""
     a = _u8(img)
     H, W = a.shape
     P, _, _ = pool_size(W, H, B, L)
@@ -157,8 +159,8 @@ def pool_filter(img, B, L, percentile):
     kept = np.zeros(max(P, 1), np.int32)
     thr = C.c_int64()
     fb = C.c_int()
-    n = lib().oracle_pool_filter(_ptr(a), W, W, H, B, L, percentile, _ptr(keys), _ptr(kept),
-                                 C.byref(thr), C.byref(fb))
+    n = lib().oracle_pool_filter(_ptr(a), W, W, H, B, L, percentile, top_k, _ptr(keys),
+                                 _ptr(kept), C.byref(thr), C.byref(fb))
     return keys[:P], kept[:n].copy(), int(thr.value), int(fb.value)
 
 
@@ -210,9 +212,9 @@ def match(img, B, L, kept, range_xy, s_p, q, n_threads=1):
 
 def make_params(n_levels=4, range_size0=16, domain_step=2, rms_threshold=8.0,
                 single_level=False, s_mode=S_PREDEFINED, grid_samples=16,
-                entropy_percentile=0.5, n_threads=1):
+                entropy_percentile=0.5, n_threads=1, pool_size=0):
     return Params(n_levels, range_size0, domain_step, rms_threshold, int(single_level),
-                  s_mode, grid_samples, entropy_percentile, n_threads)
+                  s_mode, grid_samples, entropy_percentile, n_threads, pool_size)
 
 
 def encode(img, params: Params):

@@ -25,6 +25,9 @@
  *   - the threshold is the pool's entropy percentile:
  *     thr = H_sorted_ascending[floor(p (P - 1))], keep H > thr; if that keeps
  *     nothing, keep H >= thr;
+ *   - a pool size K (Tables 1-2) keeps the K highest entropies: thr = the
+ *     (K+1)-th highest entropy, keep H > thr (ties at thr dropped); K >= P
+ *     keeps the whole pool;
  *   - isometry k = 0..3 rotates clockwise by 90k degrees; k = 4..7 mirrors
  *     left-right after rotation k - 4;
  *   - the grid S set is k / (M - 1), k = 0..M-1; s is never negative and o
@@ -118,7 +121,7 @@ static int cmp_i64(const void* a, const void* b) {
 }
 
 int oracle_pool_filter(const uint8_t* img, long pitch, int W, int H, int B, int L,
-                       double percentile, int64_t* keys, int32_t* kept,
+                       double percentile, int pool_size, int64_t* keys, int32_t* kept,
                        int64_t* thr_key, int* fallback) {
   int nx, ny;
   int P = oracle_pool_size(W, H, B, L, &nx, &ny);
@@ -133,18 +136,29 @@ int oracle_pool_filter(const uint8_t* img, long pitch, int W, int H, int B, int 
   int64_t* sorted = (int64_t*)malloc(sizeof(int64_t) * (size_t)P);
   memcpy(sorted, keys, sizeof(int64_t) * (size_t)P);
   qsort(sorted, (size_t)P, sizeof(int64_t), cmp_i64);
-  long i_h = (long)floor(percentile * (double)(P - 1));
-  if (i_h < 0) i_h = 0;
-  if (i_h > P - 1) i_h = P - 1;
-  int64_t thr = sorted[P - 1 - i_h];
+  long rank;  /* ascending key rank of the threshold */
+  int keep_all = 0;
+  if (pool_size > 0) {
+    /* Tables 1-2's pool size K: the K highest entropies are the K lowest
+     * keys, all below the key of ascending rank K */
+    rank = pool_size < P ? pool_size : P - 1;
+    keep_all = pool_size >= P;
+  } else {
+    long i_h = (long)floor(percentile * (double)(P - 1));
+    if (i_h < 0) i_h = 0;
+    if (i_h > P - 1) i_h = P - 1;
+    rank = P - 1 - i_h;
+  }
+  int64_t thr = sorted[rank];
   free(sorted);
 
   /* Keep entropy > threshold, i.e. key < thr_key. */
   int n = 0;
-  for (int d = 0; d < P; ++d)
-    if (keys[d] < thr) kept[n++] = d;
+  if (!keep_all)
+    for (int d = 0; d < P; ++d)
+      if (keys[d] < thr) kept[n++] = d;
   int fb = 0;
-  if (n == 0) { /* nothing strictly above: keep H >= thr */
+  if (n == 0) { /* nothing strictly above (or K >= P): keep H >= thr */
     fb = 1;
     for (int d = 0; d < P; ++d)
       if (keys[d] <= thr) kept[n++] = d;
@@ -331,8 +345,8 @@ int oracle_encode(const uint8_t* img, long pitch, int W, int H, const oracle_par
     int32_t* kept = (int32_t*)malloc(sizeof(int32_t) * (size_t)P);
     int64_t thr;
     int fb;
-    int n_kept = oracle_pool_filter(img, pitch, W, H, B, L, prm->entropy_percentile, keys,
-                                    kept, &thr, &fb);
+    int n_kept = oracle_pool_filter(img, pitch, W, H, B, L, prm->entropy_percentile,
+                                    prm->pool_size, keys, kept, &thr, &fb);
     int32_t sp[64], q;
     int n_s = oracle_s_set(prm->s_mode, prm->grid_samples, B, sp, &q);
     oracle_match_result* res =

@@ -38,6 +38,8 @@ typedef struct {
   int grid_samples;          /* M for ORACLE_S_GRID                       */
   double entropy_percentile; /* 0 <= p <= 1                               */
   int n_threads;             /* OpenMP threads for the range loop (>= 1)  */
+  int pool_size;             /* K > 0: keep the K highest-entropy domains
+                                (Tables 1-2 "pool size"); 0: percentile   */
 } oracle_params;
 
 /* One saved affine transformation (Sec. 2). */
@@ -86,10 +88,13 @@ void oracle_key_table(int64_t* table, int qmax);
 /* Number of pool positions for block size B and step L (Sec. 2). */
 int oracle_pool_size(int W, int H, int B, int L, int* px, int* py);
 
-/* Entropy keys of every pool position (raster order), the percentile
- * threshold and the kept list (ascending raster index).  Returns n_kept. */
+/* Entropy keys of every pool position (raster order), the threshold and the
+ * kept list (ascending raster index).  pool_size K > 0 keeps the K highest
+ * entropies (threshold = the key of ascending rank min(K, P - 1), keep
+ * key < threshold; K >= P keeps the whole pool); pool_size 0 uses the
+ * percentile.  Returns n_kept. */
 int oracle_pool_filter(const uint8_t* img, long pitch, int W, int H, int B, int L,
-                       double percentile, int64_t* keys, int32_t* kept,
+                       double percentile, int pool_size, int64_t* keys, int32_t* kept,
                        int64_t* thr_key, int* fallback);
 
 /* 2x2 sums of the 2B x 2B block at (x, y): Ds[i*B+j] (Eq. 1's decimated

@@ -54,7 +54,8 @@ def oracle_params(p):
                               domain_step=p.domain_step, rms_threshold=p.rms_threshold,
                               single_level=bool(p.single_level), s_mode=p.s_mode,
                               grid_samples=p.grid_samples,
-                              entropy_percentile=p.entropy_percentile, n_threads=8)
+                              entropy_percentile=p.entropy_percentile, n_threads=8,
+                              pool_size=p.pool_size)
 
 
 def keys_of(m, n_s):

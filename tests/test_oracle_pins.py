@@ -123,6 +123,33 @@ def test_pool_keys_positions_and_threshold():
         assert np.all(np.diff(kept) > 0)
 
 
+def test_pool_size_keeps_the_highest_entropies():
+    """Tables 1-2's pool size K: the kept set is the K domains of highest
+    entropy (scipy entropies; ties at the boundary dropped), K >= P keeps the
+    whole pool."""
+    img = synth_image(64, 48, 4, n_textured=1)
+    H, W = img.shape
+    for B, L, K in [(8, 2, 32), (4, 2, 64), (2, 1, 256), (4, 3, 7), (8, 4, 10 ** 6)]:
+        keys, kept, thr, fb = oracle.pool_filter(img, B, L, 0.5, top_k=K)
+        xs = list(range(0, W - 2 * B + 1, L))
+        ys = list(range(0, H - 2 * B + 1, L))
+        ents = np.array([scipy.stats.entropy(np.bincount(img[y:y + 2 * B, x:x + 2 * B].ravel(),
+                                                          minlength=256))
+                         for y in ys for x in xs])
+        P = len(ents)
+        if K >= P:
+            assert len(kept) == P and fb == 1
+            continue
+        # entropy of the (K+1)-th highest: keep what lies strictly above it
+        thr_h = np.sort(ents)[::-1][K]
+        strict = set(np.nonzero(ents > thr_h + 1e-9)[0].tolist())
+        near = set(np.nonzero(np.abs(ents - thr_h) <= 1e-9)[0].tolist())
+        kept_set = set(kept.tolist())
+        assert strict <= kept_set <= strict | near
+        assert len(kept) <= K
+        assert np.all(np.diff(kept) > 0)
+
+
 def test_pool_fallback_on_flat_image():
     img = np.full((32, 32), 9, np.uint8)
     keys, kept, thr, fb = oracle.pool_filter(img, 4, 2, 0.5)
