@@ -81,6 +81,11 @@ typedef struct {
   int autotune;              /* 0: default schedule; 1: time candidate
                                 schedules on first use of a shape and keep the
                                 fastest                                       */
+  int pool_size;             /* K > 0: the entropy filter keeps the K domains
+                                of highest entropy (Tables 1-2's "pool size":
+                                threshold = the (K+1)-th highest entropy, kept
+                                when strictly above, ties dropped; K >= P keeps
+                                the whole pool); 0: entropy_percentile         */
 } fic_params;
 
 typedef struct {

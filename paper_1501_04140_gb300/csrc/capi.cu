@@ -155,6 +155,7 @@ int check_params(const fic_params* p) {
   if (!(p->entropy_percentile >= 0.0 && p->entropy_percentile <= 1.0)) return FIC_EINVAL;
   if (p->precision != FIC_PREC_TENSOR && p->precision != FIC_PREC_FP32) return FIC_EINVAL;
   if (!(p->rms_threshold >= 0.0)) return FIC_EINVAL;
+  if (p->pool_size < 0) return FIC_EINVAL;
   return FIC_OK;
 }
 
@@ -313,6 +314,7 @@ int level_alloc(fic_ctx* ctx, LevelWs& w, const std::vector<fic_image>& ims, int
   w.pool.want_f32 = !tc;
   make_sset(prm.s_mode, prm.grid_samples, B, &w.pool.sset);
   w.pool.pct = prm.entropy_percentile;
+  w.pool.top_k = prm.pool_size;
   return rc ? FIC_ENOMEM : FIC_OK;
 }
 
@@ -537,6 +539,7 @@ int fic_default_params(fic_params* out) {
   p.entropy_percentile = 0.5;
   p.precision = FIC_PREC_TENSOR;
   p.autotune = 0;
+  p.pool_size = 0;
   *out = p;
   return FIC_OK;
 }
@@ -615,6 +618,7 @@ int fic_build_domain_pool(fic_ctx* ctx, const fic_image* img, int range_size,
     p->pl.want_f32 = !p->pl.want_tc;
     make_sset(params->s_mode, params->grid_samples, range_size, &p->pl.sset);
     p->pl.pct = params->entropy_percentile;
+    p->pl.top_k = params->pool_size;
     rc = pool_alloc(p->pl);
     if (!rc) rc = pool_upload(p->pl, p->staging.dev_pix, st);
     if (!rc) rc = pool_build(p->pl, ctx->dT.as<int64_t>(), st);
@@ -732,6 +736,7 @@ int fic_match_level(fic_ctx* ctx, const fic_image* img, const fic_pool* pool,
     w.pool.want_tc = src.want_tc; w.pool.want_f32 = src.want_f32;
     make_sset(params->s_mode, params->grid_samples, B, &w.pool.sset);
     w.pool.pct = src.pct;
+    w.pool.top_k = src.top_k;
     // borrowed pointers (not released by this handle)
     w.pool.img = src.img; w.pool.sel = src.sel; w.pool.slot_off = src.slot_off;
     w.pool.bpack = src.bpack; w.pool.b32 = src.b32; w.pool.dom = src.dom;

@@ -48,6 +48,7 @@ struct PoolLevel {
   bool want_tc = false, want_f32 = false;
   SSet sset{};
   double pct = 0.5;                  // entropy percentile of the threshold
+  int top_k = 0;                     // > 0: keep the top_k highest entropies instead
   int nsm = 0;                       // SMs of the device (grid sizing)
   // per position: off, keys, sd, sq; per slot: slot_off, kept, bpack, b32, dom, domf
   DevBuf off, slot_off, img, keys, sd, sq, sel, hist, kept, bpack, b32, dom, domf, scan_scratch,

@@ -252,7 +252,23 @@ int pool_prepare() {
 // threshold is the pool's entropy at percentile p: sorted ascending by
 // entropy, index floor(p (P - 1)).  Entropy ascending is key descending, so
 // the threshold is the key of ascending rank P - 1 - floor(p (P - 1)).
-__global__ void k_sel_init(const int64_t* __restrict__ off, int n_images, double pct,
+// Rank of the threshold key (ascending key order) and whether the whole pool
+// is kept: the percentile p, or Tables 1-2's pool size K (the K lowest keys
+// lie below the key of ascending rank K; K >= P keeps everything).
+__device__ inline int64_t sel_rank(int64_t P, double pct, int top_k, int* keep_all) {
+  *keep_all = 0;
+  if (P <= 0) return 0;
+  if (top_k > 0) {
+    *keep_all = top_k >= P;
+    return top_k < P ? top_k : P - 1;
+  }
+  int64_t ih = (int64_t)floor(pct * (double)(P - 1));
+  if (ih < 0) ih = 0;
+  if (ih > P - 1) ih = P - 1;
+  return P - 1 - ih;
+}
+
+__global__ void k_sel_init(const int64_t* __restrict__ off, int n_images, double pct, int top_k,
                            SelState* __restrict__ st, uint32_t* __restrict__ hist) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_images * kSelBins;
        i += gridDim.x * blockDim.x)
@@ -260,13 +276,12 @@ __global__ void k_sel_init(const int64_t* __restrict__ off, int n_images, double
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n_images) {
     int64_t P = off[i + 1] - off[i];
-    int64_t ih = (int64_t)floor(pct * (double)(P - 1));
-    if (ih < 0) ih = 0;
-    if (ih > P - 1) ih = P - 1;
+    int keep_all;
     SelState s{};
     s.prefix = 0;
-    s.rank = (P > 0) ? (P - 1 - ih) : 0;
+    s.rank = sel_rank(P, pct, top_k, &keep_all);
     s.nlt = 0;
+    s.fallback = keep_all;  // kept: key <= threshold
     st[i] = s;
   }
 }
@@ -320,7 +335,7 @@ k_sel_find(SelState* __restrict__ st, uint32_t* __restrict__ hist, int last) {
     if (last) {
       s.thr = s.prefix;
       s.nle = s.nlt + c;
-      s.fallback = (s.nlt == 0) ? 1 : 0;
+      s.fallback = (s.nlt == 0 || s.fallback) ? 1 : 0;
       s.nkept = (int32_t)(s.fallback ? s.nle : s.nlt);
     }
     st[im] = s;
@@ -356,7 +371,8 @@ constexpr int kSelWPasses = 4;  // 48 >= 45 key bits
 
 __global__ void __launch_bounds__(kSelFusedThreads)
 k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ off,
-                 const int64_t* __restrict__ slot_off, double pct, SelState* __restrict__ st,
+                 const int64_t* __restrict__ slot_off, double pct, int top_k,
+                 SelState* __restrict__ st,
                  int32_t* __restrict__ kept, unsigned int* __restrict__ umax) {
   __shared__ uint32_t hist[kSelWBins];
   __shared__ int64_t cand[kSelCand];
@@ -369,11 +385,10 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
   const int64_t o0 = off[im], P = off[im + 1] - o0;
   const int64_t* k = keys + o0;
   if (threadIdx.x == 0) {
-    int64_t ih = (int64_t)floor(pct * (double)(P - 1));
-    if (ih < 0) ih = 0;
-    if (ih > P - 1) ih = P - 1;
+    int keep_all;
     SelState z{};
-    z.rank = (P > 0) ? (P - 1 - ih) : 0;
+    z.rank = sel_rank(P, pct, top_k, &keep_all);
+    z.fallback = keep_all;  // kept: key <= threshold
     s_st = z;
     n_cand = 0;
     if (im == 0) *umax = 0;  // the packer's running maximum starts here
@@ -437,7 +452,7 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
           if (pass == kSelWPasses - 1) {
             x.thr = x.prefix;
             x.nle = x.nlt + c[u];
-            x.fallback = (x.nlt == 0) ? 1 : 0;
+            x.fallback = (x.nlt == 0 || x.fallback) ? 1 : 0;
             x.nkept = (int32_t)(x.fallback ? x.nle : x.nlt);
           }
           s_st = x;
@@ -654,10 +669,11 @@ int pool_build(PoolLevel& pl, const int64_t* d_dT, cudaStream_t st) {
   for (int i = 0; i < ni; ++i) pmax = std::max(pmax, pl.h_off[i + 1] - pl.h_off[i]);
   if (pmax <= kSelFusedMax) {
     k_select_compact<<<ni, kSelFusedThreads, 0, st>>>(pl.keys.as<int64_t>(), off,
-                                                      pl.slot_off.as<int64_t>(), pct, sel,
+                                                      pl.slot_off.as<int64_t>(), pct, pl.top_k,
+                                                      sel,
                                                       pl.kept.as<int32_t>(), pl.umax.as<unsigned int>());
   } else {
-    k_sel_init<<<ceil_div(ni * kSelBins, 256), 256, 0, st>>>(off, ni, pct, sel, hist);
+    k_sel_init<<<ceil_div(ni * kSelBins, 256), 256, 0, st>>>(off, ni, pct, pl.top_k, sel, hist);
     const int nb = (int)ceil_div64(P > 0 ? P : 1, (int64_t)kSelThreads * kSelPerThread);
     for (int pass = 0; pass < kSelPasses; ++pass) {
       const int shift = (kSelPasses - 1 - pass) * kSelBits;

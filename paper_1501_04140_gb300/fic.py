@@ -41,7 +41,7 @@ class fic_params(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("range_size0", C.c_int), ("domain_step", C.c_int),
                 ("rms_threshold", C.c_double), ("single_level", C.c_int), ("s_mode", C.c_int),
                 ("grid_samples", C.c_int), ("entropy_percentile", C.c_double),
-                ("precision", C.c_int), ("autotune", C.c_int)]
+                ("precision", C.c_int), ("autotune", C.c_int), ("pool_size", C.c_int)]
 
 
 class fic_image(C.Structure):

@@ -19,12 +19,21 @@ def test_library_exports_every_declared_function():
     assert set(names) <= set(fic._SIGS), set(names) - set(fic._SIGS)
 
 
-def test_struct_layouts_match_header():
-    # sizes the C side uses (fic_transform is shared with the oracle's codes)
-    assert C.sizeof(fic.fic_transform) == 88
-    assert C.sizeof(fic.fic_params) == 56
-    assert C.sizeof(fic.fic_level_stats) == 40
-    assert fic.TRANSFORM_DTYPE.itemsize == 88
+def test_struct_layouts_match_header(tmp_path):
+    # the binding's structs have the sizes a C compiler gives the header's
+    import os
+    import subprocess
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include "fic.h"\nint main(void) { printf("%zu %zu %zu\\n", '
+                   'sizeof(fic_transform), sizeof(fic_params), sizeof(fic_level_stats)); return 0; }\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", hdr, str(src), "-o", str(exe)], check=True)
+    c_sizes = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                              check=True).stdout.split()]
+    assert c_sizes == [C.sizeof(fic.fic_transform), C.sizeof(fic.fic_params),
+                       C.sizeof(fic.fic_level_stats)]
+    assert C.sizeof(fic.fic_transform) == 88 == fic.TRANSFORM_DTYPE.itemsize
 
 
 def test_status_strings_and_defaults():

@@ -77,6 +77,24 @@ def test_pool_parity(case, prec):
     pool.free()
 
 
+@pytest.mark.parametrize("B,L,K", [(8, 2, 32), (4, 1, 256), (16, 2, 1), (2, 2, 10 ** 6),
+                                   (8, 3, 100)])
+def test_pool_parity_pool_size(B, L, K):
+    """Tables 1-2's pool size: the K highest entropies, bit-exact with the
+    oracle (K >= P keeps the whole pool)."""
+    fic = _fic()
+    ctx = G.ctx()
+    img = synth_image(96, 64, 12, n_textured=1)
+    p = fic.default_params(domain_step=L, pool_size=K)
+    pool = ctx.build_domain_pool(G.dev(img), B, p)
+    info = pool.info()
+    keys_o, kept_o, thr_o, fb_o = oracle.pool_filter(img, B, L, 0.5, top_k=K)
+    np.testing.assert_array_equal(pool.copy(fic.FIC_POOL_KEYS), keys_o)
+    assert info["thr_key"] == thr_o and info["fallback"] == fb_o
+    np.testing.assert_array_equal(pool.copy(fic.FIC_POOL_KEPT), kept_o)
+    pool.free()
+
+
 MATCH_CASES = [
     # (W, H, seed, B, L, s_mode, grid, n_ranges or None (all))
     (64, 64, 5, 8, 2, 0, 16, None),
@@ -160,6 +178,8 @@ ENC_CASES = [
                           grid_samples=16)),
     (48, 80, 24, 1, dict(entropy_percentile=0.75, rms_threshold=5.0)),
     (64, 64, 25, 1, dict(range_size0=4, n_levels=2, domain_step=2, rms_threshold=3.0)),
+    (96, 96, 26, 1, dict(pool_size=64)),
+    (64, 64, 27, 1, dict(pool_size=32, s_mode=1, grid_samples=10)),
 ]
 
 
