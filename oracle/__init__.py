@@ -112,6 +112,10 @@ def lib():
                                         C.c_int, _P]
             L.oracle_decode.restype = C.c_int
             L.oracle_decode.argtypes = [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, _P]
+            L.oracle_quantize_o.restype = None
+            L.oracle_quantize_o.argtypes = [_P, C.c_int, C.c_int]
+            L.oracle_code_bits.restype = C.c_int64
+            L.oracle_code_bits.argtypes = [_P, C.c_int, _P, C.c_int]
             _lib = L
     return _lib
 
@@ -237,6 +241,28 @@ def decode(codes, W, H, max_iters=300, tol=1e-7):
     out = np.zeros(W * H, np.float64)
     it = lib().oracle_decode(_ptr(c), len(c), W, H, max_iters, tol, _ptr(out))
     return out.reshape(H, W), it
+
+
+def quantize_o(codes, o_bits=7):
+    """Copy of the codes with o stored in o_bits bits (the stored form)."""
+    c = np.ascontiguousarray(codes, dtype=CODE_DTYPE).copy()
+    lib().oracle_quantize_o(_ptr(c), len(c), o_bits)
+    return c
+
+
+def code_bits(stats, s_mode=S_PREDEFINED, grid_samples=16, o_bits=7):
+    """Total bits of an encode's stored form, from its per-level stats."""
+    n = len(stats)
+    st = (LevelStats * n)()
+    for i, d in enumerate(stats):
+        for f, _ in LevelStats._fields_:
+            setattr(st[i], f, d[f])
+    ns = (C.c_int * n)(*[len(s_set(s_mode, grid_samples, d["size"])[0]) for d in stats])
+    return int(lib().oracle_code_bits(st, n, ns, o_bits))
+
+
+def compression_ratio(W, H, bits):
+    return 8.0 * W * H / bits
 
 
 def to_u8(img_f64):

@@ -426,6 +426,38 @@ int oracle_encode(const uint8_t* img, long pitch, int W, int H, const oracle_par
   return overflow ? -1 : n_codes;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Stored form: quantised o and the bit count (readings in the header)       */
+/* ------------------------------------------------------------------------ */
+
+void oracle_quantize_o(oracle_code* codes, int n_codes, int o_bits) {
+  const double levels = (double)((1L << o_bits) - 1);
+  const double step = 510.0 / levels;
+  for (int c = 0; c < n_codes; ++c) {
+    double u = nearbyint((codes[c].o + 255.0) / step); /* default mode: half to even */
+    if (u < 0.0) u = 0.0;
+    if (u > levels) u = levels;
+    codes[c].o = u * step - 255.0;
+  }
+}
+
+static int ceil_log2(int64_t v) {
+  int b = 0;
+  while (((int64_t)1 << b) < v) ++b;
+  return b;
+}
+
+int64_t oracle_code_bits(const oracle_level_stats* stats, int n_levels, const int* n_s,
+                         int o_bits) {
+  int64_t bits = 0;
+  for (int l = 0; l < n_levels; ++l) {
+    if (l < n_levels - 1) bits += stats[l].n_active; /* kept or split */
+    bits += (int64_t)stats[l].n_accepted *
+            (ceil_log2(stats[l].pool_size) + 3 + ceil_log2(n_s[l]) + o_bits);
+  }
+  return bits;
+}
+
 int oracle_decode(const oracle_code* codes, int n_codes, int W, int H, int max_iters,
                   double tol, double* out) {
   double* cur = out;

@@ -127,6 +127,21 @@ void oracle_match(const uint8_t* img, long pitch, int W, int H, int B, int L,
 int oracle_encode(const uint8_t* img, long pitch, int W, int H, const oracle_params* prm,
                   oracle_code* codes, int cap, oracle_level_stats* stats);
 
+/* Stored form of the maps (the paper reports compression ratios but gives no
+ * layout; this is the reading used here):
+ *   - o is stored with `o_bits` bits, uniform over [-255, 255] (s is in
+ *     [0, 1] and the means in [0, 255]): step = 510 / (2^o_bits - 1),
+ *     o' = round((o + 255) / step) * step - 255 (round half to even);
+ *   - every range of a level above the last costs one quadtree bit (kept or
+ *     split); every saved map costs ceil(log2 P) bits of domain position
+ *     (P = the level's pool positions, which a decoder can count),
+ *     3 bits of isometry, ceil(log2 |S|) bits of s and o_bits bits of o.
+ * oracle_quantize_o replaces each code's o by o'; oracle_code_bits returns
+ * the total bits of an encode from its level statistics. */
+void oracle_quantize_o(oracle_code* codes, int n_codes, int o_bits);
+int64_t oracle_code_bits(const oracle_level_stats* stats, int n_levels, const int* n_s,
+                         int o_bits);
+
 /* Fixed-point decoder: Jacobi iteration from a flat 128 image, stopping
  * when max |delta| < tol or after max_iters.  out: W*H doubles.  Returns the
  * number of iterations done. */

@@ -423,3 +423,38 @@ def test_decoder_fixed_point_satisfies_codes():
         want = np.clip(c["s"] * T + c["o"], 0.0, 255.0)
         got = dec[c["y"]:c["y"] + B, c["x"]:c["x"] + B]
         np.testing.assert_allclose(got, want, atol=1e-8)
+
+
+# ---------------------------------------------------------------- stored form
+
+def test_quantized_offset_grid_error_and_endpoints():
+    """o stored in b bits over [-255, 255]: every value lands on the grid
+    k * step - 255, within half a step of the original, monotone, endpoints
+    exact, and quantising twice changes nothing."""
+    for b in (5, 7, 8):
+        step = 510.0 / (2 ** b - 1)
+        o = np.concatenate([np.linspace(-255, 255, 2001), [-255.0, 255.0, 0.0, 3.3, -17.25]])
+        codes = np.zeros(len(o), oracle.CODE_DTYPE)
+        codes["o"] = o
+        q1 = oracle.quantize_o(codes, b)["o"]
+        k = (q1 + 255.0) / step
+        assert np.allclose(k, np.round(k), atol=1e-9)
+        assert np.all(np.abs(q1 - o) <= step / 2 + 1e-9)
+        srt = np.argsort(o, kind="stable")
+        assert np.all(np.diff(q1[srt]) >= -1e-12)
+        assert q1[-5] == -255.0 and abs(q1[-4] - 255.0) < 1e-9
+        q2 = oracle.quantize_o(oracle.quantize_o(codes, b), b)["o"]
+        np.testing.assert_array_equal(q2, q1)
+
+
+def test_code_bits_flat_image_by_hand():
+    """Flat 64 x 64 image, T = 0: the 16 ranges of 16 x 16 are all kept at the
+    first of four levels with E = 0.  By hand: 16 quadtree bits, and per map
+    ceil(log2 289) = 9 position bits (17 x 17 positions at L = 2), 3 isometry
+    bits, 0 bits of s (|S| = 1) and 7 bits of o: 16 + 16 * 19 = 320 bits."""
+    img = np.full((64, 64), 90, np.uint8)
+    codes, stats = oracle.encode(img, oracle.make_params(rms_threshold=0.0))
+    assert len(codes) == 16 and stats[0]["pool_size"] == 289
+    bits = oracle.code_bits(stats, o_bits=7)
+    assert bits == 320
+    assert abs(oracle.compression_ratio(64, 64, bits) - 8 * 64 * 64 / 320) < 1e-12
