@@ -219,6 +219,23 @@ int fic_code_get(const fic_code* code, int image_idx, fic_transform* host_out, s
 /* Per-level statistics of one image (n_levels entries; synchronises). */
 int fic_code_stats(const fic_code* code, int image_idx, fic_level_stats* host_out, int cap);
 
+/* Stored form of the maps.  The paper reports compression ratios (Tables
+ * 1-2, "Com. rat") but states no bit layout; the layout here is a reading:
+ *   - o is stored with o_bits bits (1..16), uniform over [-255, 255]:
+ *     step = 510 / (2^o_bits - 1), o' = rint((o + 255) / step) * step - 255
+ *     (round half to even, clamped to the end points);
+ *   - every range of a level above the last costs one quadtree bit, and
+ *     every saved map ceil(log2 P) bits of domain position (P = the level's
+ *     pool positions), 3 bits of isometry, ceil(log2 |S|) bits of s and
+ *     o_bits bits of o.
+ * fic_code_quantize_o replaces o by o' in every saved map of every image
+ * (asynchronous on the code's last stream; later decodes use o').  e, e_num
+ * and o_num keep the unquantised map's values.  fic_code_bits writes the
+ * total bits of one image's stored form to *bits (synchronises); the
+ * compression ratio is 8 W H / bits.  FIC_EINVAL for o_bits outside 1..16. */
+int fic_code_quantize_o(fic_code* code, int o_bits);
+int fic_code_bits(const fic_code* code, int image_idx, int o_bits, int64_t* bits);
+
 void fic_code_free(fic_code* code);
 
 /* Timing hooks (CUDA events recorded on the encode's stream, also inside a

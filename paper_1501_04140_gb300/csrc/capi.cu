@@ -969,6 +969,40 @@ int fic_code_stats(const fic_code* code, int image_idx, fic_level_stats* host_ou
   return FIC_OK;
 }
 
+int fic_code_quantize_o(fic_code* code, int o_bits) {
+  if (!code || o_bits < 1 || o_bits > 16) return FIC_EINVAL;
+  cudaSetDevice(code->ctx->device);
+  for (int l = 0; l < code->n_levels; ++l) {
+    LevelWs& w = code->lv[l];
+    // the level's saved maps: code_off[n_images] of them
+    int rc = launch_quantize_o(w.codes.as<fic_transform>(),
+                               w.code_off.as<int64_t>() + code->n_images, w.cap, o_bits, code->st);
+    if (rc) return rc;
+  }
+  return FIC_OK;
+}
+
+int fic_code_bits(const fic_code* code, int image_idx, int o_bits, int64_t* bits) {
+  if (!code || !bits || o_bits < 1 || o_bits > 16) return FIC_EINVAL;
+  fic_level_stats st[4];
+  int rc = fic_code_stats(code, image_idx, st, 4);
+  if (rc) return rc;
+  auto ceil_log2 = [](int64_t v) {
+    int b = 0;
+    while (((int64_t)1 << b) < v) ++b;
+    return b;
+  };
+  int64_t total = 0;
+  for (int l = 0; l < code->n_levels; ++l) {
+    SSet S;
+    make_sset(code->prm.s_mode, code->prm.grid_samples, st[l].size, &S);
+    if (l < code->n_levels - 1) total += st[l].n_active;  // kept or split
+    total += (int64_t)st[l].n_accepted * (ceil_log2(st[l].pool_size) + 3 + ceil_log2(S.m) + o_bits);
+  }
+  *bits = total;
+  return FIC_OK;
+}
+
 void fic_code_free(fic_code* c) {
   if (!c) return;
   if (c->ctx) cudaSetDevice(c->ctx->device);

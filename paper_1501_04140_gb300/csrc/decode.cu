@@ -15,6 +15,31 @@
 
 namespace fic {
 
+// Stored form of o: rint((o + 255) / step) * step - 255 with
+// step = 510 / (2^b - 1), clamped, each operation rounded on its own (no
+// fused multiply-add), so that the value equals a plain sequential
+// evaluation.
+__global__ void k_quantize_o(fic_transform* __restrict__ codes, const int64_t* __restrict__ n_codes,
+                             int o_bits) {
+  const double levels = (double)((1LL << o_bits) - 1);
+  const double step = __ddiv_rn(510.0, levels);
+  const int64_t N = *n_codes;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double u = rint(__ddiv_rn(__dadd_rn(codes[i].o, 255.0), step));
+    u = u < 0.0 ? 0.0 : (u > levels ? levels : u);
+    codes[i].o = __dadd_rn(__dmul_rn(u, step), -255.0);
+  }
+}
+
+int launch_quantize_o(fic_transform* codes, const int64_t* n_codes, int64_t cap, int o_bits,
+                      cudaStream_t st) {
+  int grid = (int)ceil_div64(cap > 0 ? cap : 1, 256);
+  if (grid > 65535) grid = 65535;
+  k_quantize_o<<<grid, 256, 0, st>>>(codes, n_codes, o_bits);
+  return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
+}
+
 // Owner map: for each pixel, the code that writes it.
 __global__ void k_owner_map(const fic_transform* __restrict__ codes, int64_t n_codes, int W,
                             int32_t* __restrict__ owner) {

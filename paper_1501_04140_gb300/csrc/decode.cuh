@@ -19,6 +19,11 @@ struct DecodeWs {
 int decode_run(const fic_transform* d_codes, int64_t n_codes, int W, int H, int max_iters,
                double tol, DecodeWs& ws, uint8_t* d_out, int out_pitch, cudaStream_t st);
 
+// o of every saved map in its stored form (o_bits bits over [-255, 255]);
+// *n_codes is the device count of the level's maps.
+int launch_quantize_o(fic_transform* codes, const int64_t* n_codes, int64_t cap, int o_bits,
+                      cudaStream_t st);
+
 }  // namespace fic
 
 namespace fic {

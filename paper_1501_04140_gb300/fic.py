@@ -100,6 +100,8 @@ _SIGS = {
     "fic_code_count": (C.c_int, [_P, C.c_int, C.POINTER(C.c_size_t)]),
     "fic_code_get": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "fic_code_stats": (C.c_int, [_P, C.c_int, C.POINTER(fic_level_stats), C.c_int]),
+    "fic_code_quantize_o": (C.c_int, [_P, C.c_int]),
+    "fic_code_bits": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int64)]),
     "fic_code_free": (None, [_P]),
     "fic_code_set_profiling": (C.c_int, [_P, C.c_int]),
     "fic_code_profile": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
@@ -347,6 +349,16 @@ class Code:
         _check(load().fic_code_stats(self._h, image_idx, arr, 4), "fic_code_stats")
         nl = 1 if self.params.single_level else self.params.n_levels
         return [{f: getattr(arr[i], f) for f, _ in fic_level_stats._fields_} for i in range(nl)]
+
+    def quantize_o(self, o_bits: int = 7):
+        """Replace o by its stored form (o_bits bits) in every saved map."""
+        _check(load().fic_code_quantize_o(self._h, o_bits), "fic_code_quantize_o")
+
+    def bits(self, image_idx: int = 0, o_bits: int = 7) -> int:
+        """Total bits of one image's stored form (8 W H / bits = compression ratio)."""
+        b = C.c_int64()
+        _check(load().fic_code_bits(self._h, image_idx, o_bits, C.byref(b)), "fic_code_bits")
+        return int(b.value)
 
     def decode(self, image_idx: int = 0, max_iters: int = 300, tol: float = 1e-7, out=None,
                stream=None):

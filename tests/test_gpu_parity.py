@@ -392,3 +392,26 @@ def test_pool_parity_large_multi_kernel_select():
         assert info["thr_key"] == thr_o and info["fallback"] == fb_o
         np.testing.assert_array_equal(pool.copy(fic.FIC_POOL_KEPT), kept_o)
         pool.free()
+
+
+@pytest.mark.parametrize("o_bits", [7, 5])
+def test_stored_form_quantized_offset_and_bits(o_bits):
+    """The stored form (o in o_bits bits, the bit count behind the compression
+    ratio) equals the oracle's: quantised o bit-exact, the decoded image of the
+    quantised maps identical, the same total bits."""
+    fic = _fic()
+    ctx = G.ctx()
+    img = synth_image(96, 64, 28, n_textured=1)
+    p = fic.default_params()
+    code = ctx.encode(G.dev(img), p)
+    ref, rstats = oracle.encode(img, G.oracle_params(p))
+    np.testing.assert_array_equal(code.transforms(0)["e_num"], ref["e_num"])
+    assert code.bits(0, o_bits) == oracle.code_bits(rstats, o_bits=o_bits)
+    code.quantize_o(o_bits)
+    got = code.transforms(0)
+    refq = oracle.quantize_o(ref, o_bits)
+    np.testing.assert_array_equal(got["o"], refq["o"])
+    dec = code.decode(0)
+    ref_f, _ = oracle.decode(refq, 96, 64)
+    np.testing.assert_array_equal(dec, oracle.to_u8(ref_f))
+    code.free()
