@@ -213,6 +213,55 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ tables
+def run_tables(args):
+    """Tables 1-2's layout on synthetic stand-ins (the paper's Baboon / F16
+    are not reproduced): for pool sizes 256, 64 and 32, the proposed method
+    (Sec. 3.1's predefined S) against the entropy-only baseline (a 10-sample s
+    grid), each with the encode time (GPU, graph replay, median of steps),
+    the compression ratio of the stored form (o in 7 bits) and the PSNR of its
+    decoded image."""
+    import torch
+    from paper_1501_04140_gb300 import build, fic
+    build.build()
+    import oracle
+    from paper_1501_04140_gb300.synth import synth_image
+    ctx = fic.Context(0)
+    stream = torch.cuda.Stream()
+    images = {"smooth+edges 512 (seed 3)": synth_image(512, 512, 3, n_textured=0),
+              "textured 512 (seed 1)": synth_image(512, 512, 1, n_textured=1)}
+    rows = []
+    for name, img in images.items():
+        d = torch.from_numpy(img).cuda()
+        for K in (256, 64, 32):
+            for method, kw in (("proposed (predefined S)", dict(s_mode=fic.FIC_S_PREDEFINED)),
+                               ("entropy-based (10-sample s grid)",
+                                dict(s_mode=fic.FIC_S_GRID, grid_samples=10))):
+                p = fic.default_params(pool_size=K, **kw)
+                code = ctx.encode(d, p, stream=stream)
+                times = []
+                for s_ in range(args.warmup + args.steps):
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ctx.encode_again(code, d, p, stream=stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if s_ >= args.warmup:
+                        times.append(e0.elapsed_time(e1))
+                bits = code.bits(0, 7)
+                code.quantize_o(7)
+                psnr = oracle.psnr(img, code.decode(0))
+                rows.append({"image": name, "pool_size": K, "method": method,
+                             "encode_ms": statistics.median(times),
+                             "compression_ratio": 8.0 * img.size / bits, "psnr_db": psnr,
+                             "n_maps": code.count(0)})
+                code.free()
+    print(json.dumps({"workload": "tables", "rows": rows}))
+    return 0
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -418,13 +467,15 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=16.0,
                     help="seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="512",
-                    help="512 (the headline), batch64 or 4096 (informational runs)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["tables"], default="512",
+                    help="512 (the headline), batch64, 4096 or tables (informational runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "tables":
+        return run_tables(args)
     return run_ours(args)
 
 
