@@ -285,7 +285,8 @@ def run_ours(args):
     l2_flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def time_path(precision, steps, warmup, profile=False):
-        p = fic.default_params(precision=precision, domain_step=wl["step"])
+        p = fic.default_params(precision=precision, domain_step=wl["step"],
+                               autotune=1 if args.autotune else 0)
         with torch.cuda.stream(stream):
             code = ctx.encode(d_img, p, stream=stream)
         torch.cuda.synchronize()
@@ -467,6 +468,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=16.0,
                     help="seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the library's default schedule (by default the library times "
+                         "its schedules on the first encode and keeps the fastest)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["tables"], default="512",
                     help="512 (the headline), batch64, 4096 or tables (informational runs)")
     args = ap.parse_args()

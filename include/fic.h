@@ -78,9 +78,11 @@ typedef struct {
   int grid_samples;          /* M for FIC_S_GRID                               */
   double entropy_percentile; /* threshold = pool entropy at this percentile    */
   int precision;             /* FIC_PREC_TENSOR or FIC_PREC_FP32               */
-  int autotune;              /* 0: default schedule; 1: time candidate
-                                schedules on first use of a shape and keep the
-                                fastest                                       */
+  int autotune;              /* 0: the default schedule (4 work items per
+                                persistent CTA); 1: on a level's first eager
+                                run, time the matcher with 2, 3, 4, 6 and 8
+                                items per CTA and keep the fastest for the
+                                code's later encodes (results are unchanged) */
   int pool_size;             /* K > 0: the entropy filter keeps the K domains
                                 of highest entropy (Tables 1-2's "pool size":
                                 threshold = the (K+1)-th highest entropy, kept

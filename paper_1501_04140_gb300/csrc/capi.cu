@@ -60,6 +60,8 @@ struct LevelWs {
   DevBuf acc_cnt, rej_cnt, code_off;
   DevBuf item_off, chunks, meta, part;
   int64_t item_cap = 0, mt_cap = 0;
+  int items_per_cta = 4;                   // the plan's work items per persistent CTA
+  bool tuned = false;                      // items_per_cta chosen by timing (autotune)
   DevBuf scan_scr, total;
   void release_all() {
     DevBuf* all[] = {&pool.off,  &pool.img,   &pool.keys,   &pool.sd,    &pool.sq,     &pool.sel,
@@ -327,16 +329,21 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
   PoolLevel& pl = w.pool;
   const int ni = pl.n_images;
   const bool tc = prm.precision == FIC_PREC_TENSOR;
-  int rc = launch_range_pack(w.B, pl.img.as<ImgDev>(), w.rec.as<RangeRec>(), w.n_act.as<int64_t>(),
-                             w.cap, w.Kp, w.mom.as<RangeMom>(), w.gthr.as<uint32_t>(),
-                             tc ? w.apack.as<uint16_t>() : nullptr,
-                             tc ? nullptr : w.a32.as<float>(), st);
-  if (rc) return rc;
   const int grid = ctx->nsm;
-  k_plan<<<1, 32, 0, st>>>(ni, w.act_off.as<int64_t>(), w.act_cnt.as<int64_t>(),
-                           pl.sel.as<SelState>(), 4 * grid, w.item_cap, w.mt_cap,
-                           w.meta.as<PlanMeta>(), w.item_off.as<int64_t>(), w.chunks.as<int32_t>(),
-                           w.acc_cnt.as<int32_t>(), w.rej_cnt.as<int32_t>());
+  // range operand (also resets the ranges' shared thresholds) and the plan
+  auto pack_plan = [&](int items_per_cta) -> int {
+    int rc = launch_range_pack(w.B, pl.img.as<ImgDev>(), w.rec.as<RangeRec>(),
+                               w.n_act.as<int64_t>(), w.cap, w.Kp, w.mom.as<RangeMom>(),
+                               w.gthr.as<uint32_t>(), tc ? w.apack.as<uint16_t>() : nullptr,
+                               tc ? nullptr : w.a32.as<float>(), st);
+    if (rc) return rc;
+    k_plan<<<1, 32, 0, st>>>(ni, w.act_off.as<int64_t>(), w.act_cnt.as<int64_t>(),
+                             pl.sel.as<SelState>(), items_per_cta * grid, w.item_cap, w.mt_cap,
+                             w.meta.as<PlanMeta>(), w.item_off.as<int64_t>(),
+                             w.chunks.as<int32_t>(), w.acc_cnt.as<int32_t>(),
+                             w.rej_cnt.as<int32_t>());
+    return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
+  };
   MatchArgs a{};
   a.B = w.B;
   a.n = w.n;
@@ -362,9 +369,48 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
   a.meta = w.meta.as<PlanMeta>();
   a.part = w.part.as<Cand>();
   a.status = ctx->status.as<uint32_t>();
-  if (ev) FIC_CUDA_TRY(record_event(ev[1], st));
-  rc = tc ? launch_match_tc(a, grid, st) : launch_match_f32(a, grid, st);
+  auto match = [&]() { return tc ? launch_match_tc(a, grid, st) : launch_match_f32(a, grid, st); };
+
+  // autotune: on the level's first eager run, time the matcher with a few
+  // work-item counts per persistent CTA (every trial from freshly reset
+  // thresholds) and keep the fastest for the level's later encodes and the
+  // captured graph
+  if (prm.autotune && !w.tuned) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    FIC_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      static const int kCand[] = {2, 3, 4, 6, 8};
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      int rc = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess
+                   ? FIC_OK
+                   : FIC_ECUDA;
+      float best = INFINITY;
+      for (int cand : kCand) {
+        if (rc) break;
+        if ((rc = pack_plan(cand))) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e0, st) != cudaSuccess || (rc = match()) ||
+            cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          rc = rc ? rc : FIC_ECUDA;
+          break;
+        }
+        if (ms < best) {
+          best = ms;
+          w.items_per_cta = cand;
+        }
+      }
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      if (rc) return rc;
+      w.tuned = true;
+    }
+  }
+
+  int rc = pack_plan(w.items_per_cta);
   if (rc) return rc;
+  if (ev) FIC_CUDA_TRY(record_event(ev[1], st));
+  if ((rc = match())) return rc;
   if (ev) FIC_CUDA_TRY(record_event(ev[2], st));
   return launch_reduce_final(w.B, pl.img.as<ImgDev>(), w.rec.as<RangeRec>(), w.n_act.as<int64_t>(),
                              w.cap, w.act_off.as<int64_t>(), pl.slot_off.as<int64_t>(), ni, pl.L,

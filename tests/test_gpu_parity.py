@@ -415,3 +415,29 @@ def test_stored_form_quantized_offset_and_bits(o_bits):
     ref_f, _ = oracle.decode(refq, 96, 64)
     np.testing.assert_array_equal(dec, oracle.to_u8(ref_f))
     code.free()
+
+
+def test_autotune_keeps_results():
+    """autotune = 1 times several schedules on the first encode and keeps the
+    fastest; the maps are the same as with the default schedule, also on the
+    graph replay that follows."""
+    fic = _fic()
+    torch = G.torch_cuda()
+    ctx = G.ctx()
+    imgs = [synth_image(W, H, 70 + i, n_textured=1) for i, (W, H) in enumerate([(96, 64), (64, 64)])]
+    d = [G.dev(im) for im in imgs]
+    p0 = fic.default_params()
+    ref = ctx.encode(d, p0)
+    want = [ref.transforms(i) for i in range(2)]
+    ref.free()
+    p1 = fic.default_params(autotune=1)
+    st = torch.cuda.Stream()
+    code = ctx.encode(d, p1, stream=st)
+    torch.cuda.synchronize()
+    for i in range(2):
+        np.testing.assert_array_equal(code.transforms(i), want[i])
+    ctx.encode_again(code, d, p1, stream=st)
+    torch.cuda.synchronize()
+    for i in range(2):
+        np.testing.assert_array_equal(code.transforms(i), want[i])
+    code.free()
