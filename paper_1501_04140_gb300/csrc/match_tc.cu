@@ -35,9 +35,11 @@
 //   warps 2-3   idle (they complete the control warpgroup);
 //   warps 4-    epilogue, EG groups of four warps (four at B <= 8, two at
 //               B = 16): each warp owns the 32 TMEM lanes = 32 domains of its
-//               quarter; the groups take turns on the tiles and merge their
-//               per-range bests per item.  A warp hands its accumulator back
-//               to the MMA as soon as the tile's last chunk is in registers.
+//               quarter.  At B = 16 the groups take turns on the tiles; at
+//               B <= 8 two groups share each tile, one half of its ranges
+//               each, and the two pairs take turns.  The groups merge their
+//               per-range bests per item.  A warp hands the accumulator back
+//               to the MMA as soon as its part of the tile is in registers.
 //
 // Screening.  The float score E' / (8 q n) = p^2 u - p y, with
 // u = V / (8 q n) and y = C / n = cmax - (sum r' / n) sum Ds', screens the
@@ -121,6 +123,12 @@ struct TcCfg {
   static constexpr int CW = NKC == 1 ? 32 : 16;       // tile columns per epilogue chunk
   static constexpr int RPC = CW / 8;                  // ranges per chunk
   static constexpr int NCH = kTileRows / CW;
+  // B <= 8: two groups score each tile, a warp two of its four chunks; it
+  // loads both, hands the accumulator back, then scores them.  B = 16: one
+  // group per tile.
+  static constexpr int GPT = UNI ? 2 : 1;             // warp groups per tile
+  static constexpr int TSETS = EG / GPT;              // tiles scored at once
+  static_assert(GPT == 1 || (NCH == 2 * GPT && NKC == 1), "two chunks per warp");
   static constexpr int MRG_BYTES = Wp::EPI_WARPS * kTileRanges * 16;  // per-warp range bests
   static constexpr int SCR_BYTES = 3 * kTileRanges * 4;  // per range: w, delta, threshold
   static constexpr int OFF_B = NA * A_BYTES;
@@ -188,7 +196,6 @@ __device__ inline float thr_of(int64_t e, float inv_up, float inv_dn, float delt
 template <int B, int MODE>
 __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs a) {
   using Cf = TcCfg<B>;
-  constexpr int EG = Cf::EG;
   constexpr int n = B * B;
   constexpr int LOGN = B == 16 ? 8 : B == 8 ? 6 : B == 4 ? 4 : 2;
   constexpr int CW = Cf::CW;
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       ptx::mbar_init(&full_b[i], 1);
       // a whole-tile stage is released by the four epilogue warps that
       // score it, a K-half stage by the MMA's commit
-      ptx::mbar_init(&empty_b[i], Cf::UNI ? 4 : 1);
+      ptx::mbar_init(&empty_b[i], Cf::UNI ? 4 * Cf::GPT : 1);
     }
     for (int i = 0; i < Cf::NA; ++i) {
       ptx::mbar_init(&a_full[i], 1);
@@ -223,7 +230,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
     }
     for (int i = 0; i < Cf::NACC; ++i) {
       ptx::mbar_init(&acc_full[i], 1);
-      ptx::mbar_init(&acc_empty[i], 4);  // the four warps of the group that reads it
+      ptx::mbar_init(&acc_empty[i], 4 * Cf::GPT);  // the warps that read it
     }
     for (int i = 0; i < Cf::ND; ++i) {
       ptx::mbar_init(&d_full[i], 1);
@@ -259,7 +266,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       for (int64_t it = blockIdx.x; ok && it < items; it += gridDim.x) {
         const ItemGeo g = item_geo(a, it, CH);
         const int ab = ai % Cf::NA;
-        if (!ptx::mbar_spin(&a_empty[ab], ((ai / Cf::NA) & 1) ^ 1) || *abort_flag) {
+        if (!ptx::mbar_spin_abort(&a_empty[ab], ((ai / Cf::NA) & 1) ^ 1, abort_flag)) {
           ok = false;
           break;
         }
@@ -273,7 +280,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           if constexpr (!Cf::UNI) {
             // the tile's scoring records: a ring of their own, ND tiles ahead
             const int db = di % Cf::ND;
-            if (!ptx::mbar_spin(&d_empty[db], ((di / Cf::ND) & 1) ^ 1) || *abort_flag) {
+            if (!ptx::mbar_spin_abort(&d_empty[db], ((di / Cf::ND) & 1) ^ 1, abort_flag)) {
               ok = false;
               break;
             }
@@ -286,7 +293,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           }
           for (int kc = 0; kc < Cf::NKC; ++kc) {
             const int st = si % Cf::NST;
-            if (!ptx::mbar_spin(&empty_b[st], ((si / Cf::NST) & 1) ^ 1) || *abort_flag) {
+            if (!ptx::mbar_spin_abort(&empty_b[st], ((si / Cf::NST) & 1) ^ 1, abort_flag)) {
               ok = false;
               break;
             }
@@ -318,20 +325,25 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       for (int64_t it = blockIdx.x; ok && it < items; it += gridDim.x) {
         const ItemGeo g = item_geo(a, it, CH);
         const int rb = ai % Cf::NA;
-        if (!ptx::mbar_spin(&a_full[rb], (ai / Cf::NA) & 1) || *abort_flag) {
+        if (!ptx::mbar_spin_abort(&a_full[rb], (ai / Cf::NA) & 1, abort_flag)) {
           ok = false;
           break;
         }
         const uint8_t* sR = sA + rb * Cf::A_BYTES;
         for (int kt = 0; ok && kt < g.t1 - g.t0; ++kt) {
           const int ab = ti % Cf::NACC;
-          if (!ptx::mbar_spin(&acc_empty[ab], ((ti / Cf::NACC) & 1) ^ 1) || *abort_flag) {
+          const uint32_t pa = ((ti / Cf::NACC) & 1) ^ 1;
+          // one stage per tile: the accumulator and the stage are usually
+          // both ready, and one round trip tests the two
+          const bool ready = Cf::NKC == 1 && ptx::mbar_test_wait2(&acc_empty[ab], pa, &full_b[si % Cf::NST],
+                                                                 (si / Cf::NST) & 1);
+          if (!ready && !ptx::mbar_spin_abort(&acc_empty[ab], pa, abort_flag)) {
             ok = false;
             break;
           }
           for (int kc = 0; kc < Cf::NKC; ++kc) {
             const int st = si % Cf::NST;
-            if (!ptx::mbar_spin(&full_b[st], (si / Cf::NST) & 1) || *abort_flag) {
+            if (!ready && !ptx::mbar_spin_abort(&full_b[st], (si / Cf::NST) & 1, abort_flag)) {
               ok = false;
               break;
             }
@@ -365,7 +377,9 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
     ptx::setmaxnreg_inc<Cf::Wp::EREGS>();
     // ------------------------------------------------------------ epilogue
     // Warps 4..: quarter qd = warp % 4 of the TMEM lanes = the tile's domains
-    // qd * 32 .. qd * 32 + 31; group h takes the tiles ti = h mod EG.  Each
+    // qd * 32 .. qd * 32 + 31; group h belongs to tile set ts = h / GPT, which
+    // takes the tiles ti = ts mod TSETS, and scores the chunks of part
+    // cp = h mod GPT of those tiles' columns.  Each
     // warp keeps its best candidate per range of the item in shared memory;
     // the warps' bests merge at item end.  Per item the first epilogue warp
     // stages each range's w, rounding bound and starting threshold (the best
@@ -378,6 +392,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
     constexpr int REFRESH = 4;               // tiles between reads of the global thresholds
     const int ew = warp - kCtlWarps;
     const int h = ew >> 2;
+    const int ts = h / Cf::GPT, cp = h % Cf::GPT;
     const int qd = warp & 3;
     const int dl = qd * 32 + lane;           // tile row = domain slot in the tile
     const uint32_t epi_threads = 32 * Cf::Wp::EPI_WARPS;
@@ -430,7 +445,8 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       const uint32_t tib = ti;
       const int len = g.t1 - g.t0;
       ti += len;
-      for (int kt = (int)((h + EG - tib % EG) % EG); kt < len; kt += EG) {
+      constexpr int TSETS = Cf::TSETS;
+      for (int kt = (int)((ts + TSETS - tib % TSETS) % TSETS); kt < len; kt += TSETS) {
         const uint32_t ti = tib + kt;
         const int t = item_tile(g, kt);
         const int ab = ti % Cf::NACC;
@@ -625,25 +641,44 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           if (__any_sync(0xffffffffu, fl != 0)) slow(c, cm, scs, wr, ch, fl);
         };
 
-        // two TMEM loads in flight; the accumulator goes back to the MMA
-        // once the tile's last chunk is in registers
         uint32_t ra[32], rb[32];
-        if (ok) load(0, ra);
-#pragma unroll 1
-        for (int ch = 0; ch < Cf::NCH; ch += 2) {
+        if constexpr (Cf::GPT == 2) {
+          // both of this warp's chunks in one load round trip; the
+          // accumulator goes back to the MMA before any scoring
+          const int c0 = 2 * cp;
           if (ok) {
+            load(c0, ra);
+            load(c0 + 1, rb);
             ptx::tmem_wait(ra);
-            load(ch + 1, rb);
-            chunk(ch, ra);
-            ptx::tmem_wait(rb);
-            if (ch + 2 < Cf::NCH) load(ch + 2, ra);
+            ptx::tmem_dep(rb);
           }
-          if (ch + 2 >= Cf::NCH) {
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
+          if (ok) {
+            chunk(c0, ra);
+            chunk(c0 + 1, rb);
           }
-          if (ok) chunk(ch + 1, rb);
+        } else {
+          // two TMEM loads in flight; the accumulator goes back to the MMA
+          // once the tile's last chunk is in registers
+          if (ok) load(0, ra);
+#pragma unroll 1
+          for (int ch = 0; ch < Cf::NCH; ch += 2) {
+            if (ok) {
+              ptx::tmem_wait(ra);
+              load(ch + 1, rb);
+              chunk(ch, ra);
+              ptx::tmem_wait(rb);
+              if (ch + 2 < Cf::NCH) load(ch + 2, ra);
+            }
+            if (ch + 2 >= Cf::NCH) {
+              ptx::tc_fence_before();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
+            }
+            if (ok) chunk(ch + 1, rb);
+          }
         }
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(rec_empty);

@@ -74,6 +74,23 @@ __device__ inline bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking probe of two phases in one shared-memory round trip: true when
+// both have completed.
+__device__ inline bool mbar_test_wait2(uint64_t* bar0, uint32_t parity0, uint64_t* bar1,
+                                       uint32_t parity1) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q, [%3], %4;\n\t"
+      "and.pred p, p, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar0)), "r"(parity0), "r"(smem_u32(bar1)), "r"(parity1)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait by spinning on test_wait (the thread never suspends): for the
 // single-thread producer and MMA issuer, whose wake-up latency sits on the
 // pipeline's critical path.
@@ -83,6 +100,18 @@ __device__ inline bool mbar_spin(uint64_t* bar, uint32_t parity) {
   for (uint32_t i = 0;; ++i) {
     if (mbar_test_wait(bar, parity)) return true;
     if ((i & 255) == 255 && global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+// mbar_spin that also gives up once `abort` is set; the flag is read only
+// while the phase is still pending, so a wait that is already satisfied costs
+// one round trip.
+__device__ inline bool mbar_spin_abort(uint64_t* bar, uint32_t parity, const volatile int* abort) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_test_wait(bar, parity)) return true;
+    if ((i & 255) == 255 && (*abort || global_ns() - t0 > kWaitLimitNs)) return false;
   }
 }
 
