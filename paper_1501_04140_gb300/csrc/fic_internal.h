@@ -57,11 +57,13 @@ struct PoolLevel {
 
 // Runs of the sliding pool statistics: along a row of pool positions, the
 // positions whose 2x2 cell grid shares a phase (every position for even L,
-// every other one for odd L), kPoolRun at a time.
+// every other one for odd L), kPoolRun at a time (kPoolRunWarp at B = 16,
+// where a warp slides one window).
 constexpr int kPoolRun = 4;
+constexpr int kPoolRunWarp = 8;
 __host__ __device__ inline int pool_run_step(int L) { return (L & 1) ? 2 : 1; }
 __host__ __device__ inline int pool_run_len(int B, int L) {
-  return pool_run_step(L) * L >= 2 * B ? 1 : kPoolRun;
+  return pool_run_step(L) * L >= 2 * B ? 1 : B == 16 ? kPoolRunWarp : kPoolRun;
 }
 // runs of one row of px positions (phase class 0 first)
 __host__ __device__ inline int pool_runs_per_row(int px, int B, int L) {

@@ -232,6 +232,120 @@ k_pool_stats_lane(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ o
   }
 }
 
+// B = 16: one warp per run, the window's 32 pixel columns (then, sliding,
+// its 32 pixel rows) on the 32 lanes and one 256-bin histogram per warp in
+// shared memory.  Each atomic returns the bin's count before it, so every
+// lane adds the exact key change of its own update (dT[c + 1] on an
+// increment from c, -dT[c] on a decrement from c) and the lanes' sums
+// telescope to the key of the final counts whatever order the atomics take.
+// A cell's 2x2 sum is two lanes' column (row) pairs, joined by a shuffle.
+constexpr int kPoolWarpThreads = 256;
+
+__global__ void __launch_bounds__(kPoolWarpThreads)
+k_pool_stats_warp16(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
+                    const int64_t* __restrict__ run_off, int n_images, int L,
+                    const int64_t* __restrict__ dT_g, int64_t* __restrict__ keys,
+                    int32_t* __restrict__ sd, int32_t* __restrict__ sq) {
+  constexpr int B = 16, W = 2 * B, N4 = 4 * B * B, WARPS = kPoolWarpThreads / 32;
+  __shared__ int64_t dT[N4 + 1];
+  __shared__ uint32_t hist[WARPS][256];
+  for (int i = threadIdx.x; i <= N4; i += blockDim.x) dT[i] = dT_g[i];
+  for (int i = threadIdx.x; i < WARPS * 256; i += blockDim.x) (&hist[0][0])[i] = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* h = hist[warp];
+  const int step = pool_run_step(L), R = pool_run_len(B, L), d = step * L;
+  const int64_t total = run_off[n_images];
+  // (warp-uniform loop: every lane takes part in the shuffles)
+  for (int64_t gr = (int64_t)blockIdx.x * WARPS + warp; gr < total;
+       gr += (int64_t)gridDim.x * WARPS) {
+    const int im = find_segment(run_off, n_images, gr);
+    const ImgDev I = imgs[im];
+    const int rpr = pool_runs_per_row(I.px, B, L);
+    const int64_t lr = gr - run_off[im];
+    const int row = (int)(lr / rpr);
+    int rem = (int)(lr % rpr), cls = 0;
+    const int r0 = ((I.px + step - 1) / step + R - 1) / R;  // runs of phase class 0
+    if (rem >= r0) {
+      cls = 1;
+      rem -= r0;
+    }
+    int i = cls + step * rem * R;  // first position of the run (x index)
+    int x0 = i * L;
+    const int pitch = I.pitch;
+    const uint8_t* base = I.pix + (int64_t)(row * L) * pitch;
+    int64_t key = 0;  // this lane's share of the key and moments
+    int s = 0, s2 = 0;
+    auto emit = [&](int64_t g) {
+      int64_t k = key;
+      int a = s, b = s2;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        k += __shfl_xor_sync(0xffffffffu, k, o);
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+      }
+      if (lane == 0) {
+        keys[g] = k;
+        sd[g] = a;
+        sq[g] = b;
+      }
+    };
+    // the run's first window: lane = pixel column, two rows per step
+    for (int r = 0; r < W; r += 2) {
+      const uint8_t* p = base + (int64_t)r * pitch + x0 + lane;
+      const int a = p[0], b = p[pitch];
+      key += dT[atomicAdd(&h[a], 1u) + 1];
+      key += dT[atomicAdd(&h[b], 1u) + 1];
+      const int col = a + b;
+      const int ds = col + __shfl_xor_sync(0xffffffffu, col, 1);
+      if (!(lane & 1)) {
+        s += ds;
+        s2 += ds * ds;
+      }
+    }
+    int64_t g = off[im] + (int64_t)row * I.px + i;
+    emit(g);
+    // next positions: lane = pixel row; the d columns that leave, the d that enter
+    const uint8_t* pr = base + (int64_t)lane * pitch;
+    // column pairs as 2-byte loads where they start on even addresses (x0
+    // keeps its parity: d is even)
+    const bool pairs = ((((uintptr_t)I.pix) | (uintptr_t)pitch | (uintptr_t)x0) & 1) == 0;
+    for (int m = 1; m < R; ++m) {
+      i += step;
+      if (i >= I.px) break;
+      for (int cc = 0; cc < d; cc += 2) {
+        int o0, o1, n0, n1;
+        if (pairs) {
+          const uchar2 o = *(const uchar2*)(pr + x0 + cc), nw = *(const uchar2*)(pr + x0 + W + cc);
+          o0 = o.x, o1 = o.y, n0 = nw.x, n1 = nw.y;
+        } else {
+          o0 = pr[x0 + cc], o1 = pr[x0 + cc + 1];
+          n0 = pr[x0 + W + cc], n1 = pr[x0 + W + cc + 1];
+        }
+        key -= dT[atomicSub(&h[o0], 1u)];
+        key -= dT[atomicSub(&h[o1], 1u)];
+        key += dT[atomicAdd(&h[n0], 1u) + 1];
+        key += dT[atomicAdd(&h[n1], 1u) + 1];
+        const int ro = o0 + o1, rn = n0 + n1;
+        const int dso = ro + __shfl_xor_sync(0xffffffffu, ro, 1);
+        const int dsn = rn + __shfl_xor_sync(0xffffffffu, rn, 1);
+        if (!(lane & 1)) {
+          s += dsn - dso;
+          s2 += dsn * dsn - dso * dso;
+        }
+      }
+      x0 += d;
+      g += step;
+      emit(g);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < 256; b += 32) h[b + lane] = 0;
+    __syncwarp();
+  }
+}
+
 template <int B>
 static int prepare_pool_B() {
   return cudaFuncSetAttribute(k_pool_stats_lane<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -240,11 +354,9 @@ static int prepare_pool_B() {
              : 1;
 }
 
-// Opt the sliding statistics kernels in to their shared memory (per device).
-int pool_prepare() {
-  return (prepare_pool_B<16>() | prepare_pool_B<8>() | prepare_pool_B<4>() | prepare_pool_B<2>())
-             ? FIC_ECUDA
-             : FIC_OK;
+// The sliding statistics kernels' shared memory.
+static int prepare_stats() {
+  return prepare_pool_B<16>() | prepare_pool_B<8>() | prepare_pool_B<4>() | prepare_pool_B<2>();
 }
 
 // ---------------------------------------------------------------- exact percentile
@@ -357,14 +469,29 @@ __global__ void k_sel_bases(SelState* st, int n_images) {
 // block per image, for pools of at most kSelFusedMax positions.  Digits are
 // 12 bits wide (4096 shared-memory bins; keys are below 2^45): the entropy
 // keys of a pool crowd into a narrow band, and wide digits spread them so
-// the bins' atomics rarely collide.  Two passes read the keys from L2; the
+// the bins' atomics rarely collide.
+//
+// Candidates.  Pools of up to kSelCand keys are copied to shared memory
+// whole.  Pools of up to kSelSampleMax keys first sort an evenly strided
+// sample of kSelSample keys and take the sample keys lo, hi kSelMargin
+// sample ranks below and above the target's estimated sample rank; one pass
+// over the keys counts those below lo and gathers those in [lo, hi].  When
+// the target rank falls among the gathered keys (it does unless the sample
+// misjudges it by more than the margin, about four standard deviations) the
+// radix passes run on them alone, starting from the count below lo; all keys
+// equal to the threshold lie in [lo, hi], so the counts stay exact.
+// Otherwise (and for larger pools) two passes read the keys from L2; the
 // second also gathers the keys that share the top digit, so the last two
 // passes usually run on shared memory alone.  The compaction then gives each
 // warp a contiguous run of positions: a counting sweep, a scan of the 32 warp
 // totals, and an ordered write with ballot ranks.
 constexpr int kSelFusedThreads = 1024;
 constexpr int64_t kSelFusedMax = (int64_t)1 << 20;
-constexpr int kSelCand = 3584;  // keeps the block under 48 KB of static shared memory
+constexpr int kSelCand = 12288;         // candidate keys (dynamic shared memory)
+constexpr int kSelSample = 1024;        // sample keys (dynamic shared memory)
+constexpr int kSelMargin = 64;          // sample ranks on each side of the estimate
+constexpr int64_t kSelSampleMax = 81920;  // about 10300 candidates expected at most
+constexpr int kSelDynBytes = (kSelCand + kSelSample) * 8;
 constexpr int kSelWBits = 12;
 constexpr int kSelWBins = 1 << kSelWBits;
 constexpr int kSelWPasses = 4;  // 48 >= 45 key bits
@@ -375,8 +502,11 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
                  SelState* __restrict__ st,
                  int32_t* __restrict__ kept, unsigned int* __restrict__ umax) {
   __shared__ uint32_t hist[kSelWBins];
-  __shared__ int64_t cand[kSelCand];
+  extern __shared__ int64_t sel_dyn[];
+  int64_t* cand = sel_dyn;               // kSelCand keys
+  int64_t* samp = sel_dyn + kSelCand;    // kSelSample keys
   __shared__ int n_cand;
+  __shared__ unsigned long long n_below;
   __shared__ int sw[32];
   __shared__ int wtot[32];
   __shared__ SelState s_st;
@@ -391,9 +521,76 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
     z.fallback = keep_all;  // kept: key <= threshold
     s_st = z;
     n_cand = 0;
+    n_below = 0;
     if (im == 0) *umax = 0;  // the packer's running maximum starts here
   }
+  __syncthreads();
   bool in_smem = false;
+  if (P <= kSelCand) {  // the whole pool as candidates
+    for (int64_t g = threadIdx.x; g < P; g += blockDim.x) cand[g] = __ldg(k + g);
+    if (threadIdx.x == 0) n_cand = (int)P;
+    in_smem = true;
+  } else if (P <= kSelSampleMax) {
+    for (int j = threadIdx.x; j < kSelSample; j += blockDim.x)
+      samp[j] = __ldg(k + (int64_t)j * P / kSelSample);
+    __syncthreads();
+    // bitonic sort of the sample, ascending
+    for (int kk = 2; kk <= kSelSample; kk <<= 1)
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int t = threadIdx.x; t < kSelSample / 2; t += blockDim.x) {
+          const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1)), ip = i + j;
+          const int64_t a = samp[i], b = samp[ip];
+          if ((a > b) == ((i & kk) == 0)) {
+            samp[i] = b;
+            samp[ip] = a;
+          }
+        }
+        __syncthreads();
+      }
+    const int64_t rank0 = s_st.rank;
+    const int ts = (int)(rank0 * kSelSample / P);
+    const int64_t lo = ts - kSelMargin >= 0 ? samp[ts - kSelMargin] : INT64_MIN;
+    const int64_t hi = ts + kSelMargin < kSelSample ? samp[ts + kSelMargin] : INT64_MAX;
+    // (warp-uniform loop: the lanes of a warp append together)
+    int below = 0;
+    constexpr int U = 8;
+    for (int64_t gb = (int64_t)warp * 32; gb < P; gb += (int64_t)U * blockDim.x) {
+      int64_t kk[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t g = gb + (int64_t)u * blockDim.x + lane;
+        kk[u] = g < P ? __ldg(k + g) : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool in = kk[u] >= 0 && kk[u] >= lo && kk[u] <= hi;  // (-1: past the end)
+        below += kk[u] >= 0 && kk[u] < lo;
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (m) {
+          int b0 = 0;
+          if (lane == 0) b0 = atomicAdd(&n_cand, __popc(m));
+          b0 = __shfl_sync(0xffffffffu, b0, 0);
+          const int i = b0 + __popc(m & ((1u << lane) - 1u));
+          if (in && i < kSelCand) cand[i] = kk[u];
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
+    if (lane == 0) atomicAdd(&n_below, (unsigned long long)below);
+    __syncthreads();
+    const int64_t nb = (int64_t)n_below, nc = n_cand;
+    in_smem = nc <= kSelCand && nb <= rank0 && rank0 < nb + nc;  // uniform
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (in_smem) {
+        s_st.rank = rank0 - nb;
+        s_st.nlt = nb;
+      } else {
+        n_cand = 0;  // the L2 passes gather afresh
+      }
+    }
+  }
   constexpr int BPT = kSelWBins / kSelFusedThreads;  // bins per thread in the scan
   for (int pass = 0; pass < kSelWPasses; ++pass) {
     const int shift = (kSelWPasses - 1 - pass) * kSelWBits;
@@ -504,6 +701,15 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
   if (threadIdx.x == 0) st[im] = s_st;
 }
 
+// Opt the pool kernels in to their shared memory (once per device, before any
+// launch or stream capture).
+int pool_prepare() {
+  const bool ok = prepare_stats() == 0 &&
+                  cudaFuncSetAttribute(k_select_compact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSelDynBytes) == cudaSuccess;
+  return ok ? FIC_OK : FIC_ECUDA;
+}
+
 struct KeptCompact {
   const int64_t* keys;
   const int64_t* off;
@@ -554,44 +760,74 @@ __device__ inline int64_t bpack_index(int64_t slot, int e) {
          (ek & 7);
 }
 
+// One thread per (kept domain, 8-element K group): the group's 8 downsampled
+// values Ds - 512 (each the sum of a 2x2 pixel block, read as two pixel
+// pairs) go out as one 16-byte store of f16; the group-0 thread also writes
+// the domain's records.
+constexpr int kPackThreads = 256;
+
 template <int B>
-__global__ void __launch_bounds__(PoolGeom<B>::threads)
+__global__ void __launch_bounds__(kPackThreads)
 k_pack_domains(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
                const int64_t* __restrict__ slot_off, int n_images, int L,
                const SelState* __restrict__ st, const int32_t* __restrict__ kept,
                const int32_t* __restrict__ sd, const int32_t* __restrict__ sq, SSet S,
                uint16_t* __restrict__ bpack, float* __restrict__ b32, DomRec* __restrict__ dom,
                float* __restrict__ domf, unsigned int* __restrict__ umax) {
-  using Gm = PoolGeom<B>;
-  constexpr int G = Gm::G;
   constexpr int n = B * B;
   constexpr int Kp = PackGeom<B>::Kp;
-  const int grp = threadIdx.x / G, gl = threadIdx.x % G;
+  constexpr int NG = Kp / 8;  // 16-byte groups per operand row
   __shared__ unsigned int s_umax;
   if (threadIdx.x == 0) s_umax = 0;
   __syncthreads();
   const int64_t S_tot = slot_off[n_images];
-  for (int64_t slot = (int64_t)blockIdx.x * Gm::GPB + grp; slot < S_tot;
-       slot += (int64_t)gridDim.x * Gm::GPB) {
+  for (int64_t w = (int64_t)blockIdx.x * kPackThreads + threadIdx.x; w < S_tot * NG;
+       w += (int64_t)gridDim.x * kPackThreads) {
+    const int64_t slot = w / NG;
+    const int g = (int)(w % NG);
     const int im = find_segment(slot_off, n_images, slot);
     const int64_t j = slot - slot_off[im];
     if (j >= st[im].nkept) continue;
     const ImgDev I = imgs[im];
     const int32_t pos = kept[slot];
-    const int64_t gpos = off[im] + pos;
     const int x0 = (pos % I.px) * L, y0 = (pos / I.px) * L;
-    uint8_t* tile_blk = bpack ? (uint8_t*)bpack + (slot >> 7) * (int64_t)tc_tile_bytes(B) : nullptr;
-    uint16_t* tile_op = (uint16_t*)tile_blk;
-    for (int c = gl; c < n; c += G) {
-      const int ci = c / B, cj = c % B;
-      const uint8_t* p = I.pix + (int64_t)(y0 + 2 * ci) * I.pitch + (x0 + 2 * cj);
-      const int ds = p[0] + p[1] + p[I.pitch] + p[I.pitch + 1];
-      if (bpack) tile_op[bpack_index<B>(slot & 127, c)] = f16_bits(ds - 512);
-      if (b32) b32[slot * n + c] = (float)(ds - 512);
+    // pixel pairs as 2-byte loads where every pair starts on an even address
+    const bool pairs = ((((uintptr_t)I.pix) | (uintptr_t)I.pitch | (uintptr_t)x0) & 1) == 0;
+    int v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = 8 * g + u;
+      v[u] = 0;  // K padding (B = 2: K = 4 of 16)
+      if (e < n) {
+        const int ci = e / B, cj = e % B;
+        const uint8_t* p = I.pix + (int64_t)(y0 + 2 * ci) * I.pitch + (x0 + 2 * cj);
+        int ds;
+        if (pairs) {
+          const uchar2 a = *(const uchar2*)p;
+          const uchar2 b = *(const uchar2*)(p + I.pitch);
+          ds = a.x + a.y + b.x + b.y;
+        } else {
+          ds = p[0] + p[1] + p[I.pitch] + p[I.pitch + 1];
+        }
+        v[u] = ds - 512;
+      }
     }
-    if (bpack && n < Kp)  // zero the K padding (B = 2: K = 4 of 16)
-      for (int c = n + gl; c < Kp; c += G) tile_op[bpack_index<B>(slot & 127, c)] = 0;
-    if (gl == 0) {
+    uint8_t* tile_blk = bpack ? (uint8_t*)bpack + (slot >> 7) * (int64_t)tc_tile_bytes(B) : nullptr;
+    if (bpack) {
+      uint4 q;
+      q.x = f16_bits(v[0]) | ((uint32_t)f16_bits(v[1]) << 16);
+      q.y = f16_bits(v[2]) | ((uint32_t)f16_bits(v[3]) << 16);
+      q.z = f16_bits(v[4]) | ((uint32_t)f16_bits(v[5]) << 16);
+      q.w = f16_bits(v[6]) | ((uint32_t)f16_bits(v[7]) << 16);
+      *(uint4*)((uint16_t*)tile_blk + bpack_index<B>(slot & 127, 8 * g)) = q;
+    }
+    if (b32) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (8 * g + u < n) b32[slot * n + 8 * g + u] = (float)v[u];
+    }
+    if (g == 0) {
+      const int64_t gpos = off[im] + pos;
       const int64_t s = sd[gpos], s2 = sq[gpos];
       DomRec r;
       r.v = (int64_t)n * s2 - s * s;
@@ -641,6 +877,14 @@ static int pool_build_B(PoolLevel& pl, const int64_t* d_dT, cudaStream_t st) {
   const int ni = pl.n_images;
   const int nsm = pl.nsm > 0 ? pl.nsm : 148;
   const int64_t runs = pl.h_run_off[ni];
+  if constexpr (B == 16) {
+    const int64_t blocks = ceil_div64(runs > 0 ? runs : 1, kPoolWarpThreads / 32);
+    const int grid = (int)(blocks < (int64_t)nsm * 8 ? blocks : (int64_t)nsm * 8);
+    k_pool_stats_warp16<<<grid, kPoolWarpThreads, 0, st>>>(
+        pl.img.as<ImgDev>(), pl.off.as<int64_t>(), pl.run_off.as<int64_t>(), ni, pl.L, d_dT,
+        pl.keys.as<int64_t>(), pl.sd.as<int32_t>(), pl.sq.as<int32_t>());
+    return FIC_OK;
+  }
   const int64_t blocks = ceil_div64(runs > 0 ? runs : 1, kPoolLaneThreads);
   const int grid = (int)(blocks < (int64_t)nsm * 3 ? blocks : (int64_t)nsm * 3);
   k_pool_stats_lane<B><<<grid, kPoolLaneThreads, PoolLaneSmem<B>::BYTES, st>>>(
@@ -668,7 +912,7 @@ int pool_build(PoolLevel& pl, const int64_t* d_dT, cudaStream_t st) {
   int64_t pmax = 0;
   for (int i = 0; i < ni; ++i) pmax = std::max(pmax, pl.h_off[i + 1] - pl.h_off[i]);
   if (pmax <= kSelFusedMax) {
-    k_select_compact<<<ni, kSelFusedThreads, 0, st>>>(pl.keys.as<int64_t>(), off,
+    k_select_compact<<<ni, kSelFusedThreads, kSelDynBytes, st>>>(pl.keys.as<int64_t>(), off,
                                                       pl.slot_off.as<int64_t>(), pct, pl.top_k,
                                                       sel,
                                                       pl.kept.as<int32_t>(), pl.umax.as<unsigned int>());
@@ -692,10 +936,10 @@ int pool_build(PoolLevel& pl, const int64_t* d_dT, cudaStream_t st) {
   float* b32 = pl.want_f32 ? pl.b32.as<float>() : nullptr;
 #define FIC_PACK(BB)                                                                           \
   {                                                                                            \
-    using Gm = PoolGeom<BB>;                                                                   \
-    const int64_t groups = ceil_div64(pl.S_tot > 0 ? pl.S_tot : 1, Gm::GPB);                  \
-    const int grid = (int)(groups < (int64_t)nsm * 16 ? groups : (int64_t)nsm * 16);          \
-    k_pack_domains<BB><<<grid, Gm::threads, 0, st>>>(                                          \
+    const int64_t work = (pl.S_tot > 0 ? pl.S_tot : 1) * (PackGeom<BB>::Kp / 8);              \
+    const int64_t blocks = ceil_div64(work, kPackThreads);                                     \
+    const int grid = (int)(blocks < (int64_t)nsm * 16 ? blocks : (int64_t)nsm * 16);          \
+    k_pack_domains<BB><<<grid, kPackThreads, 0, st>>>(                                         \
         pl.img.as<ImgDev>(), off, pl.slot_off.as<int64_t>(), ni, pl.L, sel,                    \
         pl.kept.as<int32_t>(),                                                                 \
         pl.sd.as<int32_t>(), pl.sq.as<int32_t>(), pl.sset, bp, b32, pl.dom.as<DomRec>(),       \
