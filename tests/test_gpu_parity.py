@@ -394,6 +394,50 @@ def test_pool_parity_large_multi_kernel_select():
         pool.free()
 
 
+# (W, H, seed, B, L, percentile, pool size K, extra pitch): pools between the
+# shared-memory sizes of the one-block select -- up to 12288 keys whole, up to
+# 81920 through two sample splitters, above that two passes over L2 -- at
+# B = 16 (one warp per sliding run) and below; odd L (every other position
+# per run, odd x offsets) and an odd row pitch (single-byte pixel loads).
+MEDIUM_POOLS = [
+    (512, 512, 11, 16, 2, 0.5, 0, 0),      # 58081 positions: sample splitters
+    (512, 512, 12, 16, 2, 0.5, 20000, 0),  # the same path, top-K
+    (320, 304, 13, 16, 1, 0.3, 0, 1),      # 78897, odd L, pitch 321
+    (304, 256, 14, 16, 3, 0.9, 0, 0),      # 6825, odd L: whole pool in shared memory
+    (384, 384, 15, 8, 1, 0.5, 0, 0),       # 136161: two L2 passes
+    (296, 296, 16, 4, 1, 0.75, 0, 3),      # 83521: two L2 passes, pitch 299
+]
+
+
+@pytest.mark.parametrize("case", range(len(MEDIUM_POOLS)))
+def test_pool_parity_medium(case):
+    """Keys, threshold, kept list and moments of medium pools match the oracle
+    bit-exactly on every path of the one-block select."""
+    fic = _fic()
+    W, H, seed, B, L, pct, K, pad = MEDIUM_POOLS[case]
+    img = synth_image(W, H, seed, n_textured=1)
+    ctx = G.ctx()
+    p = fic.default_params(domain_step=L, entropy_percentile=pct, pool_size=K)
+    dev = G.dev(np.pad(img, ((0, 0), (0, pad))))[:, :W]  # row pitch W + pad
+    assert dev.stride(0) == W + pad
+    pool = ctx.build_domain_pool(dev, B, p)
+    info = pool.info()
+    keys_o, kept_o, thr_o, fb_o = oracle.pool_filter(img, B, L, pct, top_k=K)
+    P, px, py = oracle.pool_size(W, H, B, L)
+    assert info["pool_size"] == P and info["px"] == px and info["py"] == py
+    np.testing.assert_array_equal(pool.copy(fic.FIC_POOL_KEYS), keys_o)
+    assert info["thr_key"] == thr_o and info["fallback"] == fb_o
+    kept = pool.copy(fic.FIC_POOL_KEPT)
+    np.testing.assert_array_equal(kept, kept_o)
+    sums = pool.copy(fic.FIC_POOL_SUMS)
+    sq = pool.copy(fic.FIC_POOL_SQSUMS)
+    for j in range(0, len(kept_o), max(1, len(kept_o) // 200)):
+        d = int(kept_o[j])
+        Ds = oracle.decimate(img, (d % px) * L, (d // px) * L, B)
+        assert sums[j] == Ds.sum() and sq[j] == (Ds * Ds).sum()
+    pool.free()
+
+
 @pytest.mark.parametrize("o_bits", [7, 5])
 def test_stored_form_quantized_offset_and_bits(o_bits):
     """The stored form (o in o_bits bits, the bit count behind the compression
