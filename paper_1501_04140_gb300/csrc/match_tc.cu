@@ -641,25 +641,79 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           if (__any_sync(0xffffffffu, fl != 0)) slow(c, cm, scs, wr, ch, fl);
         };
 
-        uint32_t ra[32], rb[32];
         if constexpr (Cf::GPT == 2) {
-          // both of this warp's chunks in one load round trip; the
-          // accumulator goes back to the MMA before any scoring
+          // both of this warp's chunks in one load round trip, screened down
+          // to per-range maxima, scores and flags; the rare exact pass reads
+          // a flagged range's 8 correlations from tensor memory again, so no
+          // correlation stays in registers past the screen, and the
+          // accumulator goes back to the MMA after it (each tile set has two
+          // accumulators, so the MMA fills the other one meanwhile)
+          constexpr int R2 = 2 * RPC;
           const int c0 = 2 * cp;
+          float cm[R2], scs[R2];
+          uint32_t fl = 0;
           if (ok) {
-            load(c0, ra);
-            load(c0 + 1, rb);
-            ptx::tmem_wait(ra);
-            ptx::tmem_dep(rb);
+            uint32_t ra[32], rb[32];
+            ptx::tmem_ld64_wait(tb + c0 * 32, ra, rb);
+            const float4 wa = *(const float4*)(sW + 4 * c0), wb = *(const float4*)(sW + 4 * c0 + 4);
+            const float4 ta = *(const float4*)(sThr + 4 * c0), tb4 = *(const float4*)(sThr + 4 * c0 + 4);
+            const float wv[R2] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+            const float tv[R2] = {ta.x, ta.y, ta.z, ta.w, tb4.x, tb4.y, tb4.z, tb4.w};
+#pragma unroll
+            for (int j = 0; j < R2; ++j) {
+              float v[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u)
+                v[u] = __uint_as_float(j < RPC ? ra[8 * j + u] : rb[8 * (j - RPC) + u]);
+              fl |= screen(v, wv[j], tv[j], cm[j], scs[j]) << j;
+            }
+          }
+          if (!dvalid) fl = 0;
+          if (__any_sync(0xffffffffu, fl != 0)) {
+            const DomRec dr = sDom[dl];
+#pragma unroll 1
+            for (int j = 0; j < R2; ++j) {
+              const bool mine = (fl >> j) & 1u;
+              if (!__any_sync(0xffffffffu, mine)) continue;
+              const int r = c0 * RPC + j;
+              // (selects, not indexing: the arrays stay in registers)
+              float cmj = cm[0], scj = scs[0];
+#pragma unroll
+              for (int u = 1; u < R2; ++u)
+                if (j == u) cmj = cm[u], scj = scs[u];
+              float mn = mine ? scj : INFINITY;
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+              const float lim = __fadd_ru(mn, 2.0f * sDelta[r]);
+              const bool need = mine && scj <= lim;
+              const unsigned bal = __ballot_sync(0xffffffffu, need);
+              float v[8];
+              ptx::tmem_ld8_wait(tb + c0 * 32 + 8 * j, v);
+              int64_t be = INT64_MAX, bk = INT64_MAX;
+              if (need) pair_exact(v, cmj, sW[r], dr, be, bk);
+              if (__popc(bal) == 1) {
+                const int src = __ffs(bal) - 1;
+                be = __shfl_sync(0xffffffffu, be, src);
+                bk = __shfl_sync(0xffffffffu, bk, src);
+              } else {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                  const int64_t e2 = __shfl_xor_sync(0xffffffffu, be, o);
+                  const int64_t k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+                  if (e2 < be || (e2 == be && k2 < bk)) {
+                    be = e2;
+                    bk = k2;
+                  }
+                }
+              }
+              resolve(r, be, bk);
+            }
           }
           ptx::tc_fence_before();
           __syncwarp();
           if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
-          if (ok) {
-            chunk(c0, ra);
-            chunk(c0 + 1, rb);
-          }
         } else {
+          uint32_t ra[32], rb[32];
           // two TMEM loads in flight; the accumulator goes back to the MMA
           // once the tile's last chunk is in registers
           if (ok) load(0, ra);
