@@ -494,6 +494,20 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           }
         };
 
+        // float score of a pair from its largest correlation and the range's w
+        auto score = [&](float cmax, float wr) -> float {
+          const float y = fmaf(nX, wr, cmax);
+          if constexpr (MODE == MODE_GRID) {
+            float p = rintf(y * F1);
+            p = fminf(fmaxf(p, 0.f), qf);
+            return p * fmaf(p, F0, -y);
+          } else if constexpr (MODE == MODE_M2) {
+            return fminf(fmaf(-p0f, y, F0), fmaf(-p1f, y, F1));
+          } else {
+            return fmaf(-p0f, y, F0);
+          }
+        };
+
         // float screen of one (domain, range) pair: the maximum of the range's
         // 8 isometry correlations, then the best score over S against the
         // range's threshold
@@ -641,54 +655,78 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           if (__any_sync(0xffffffffu, fl != 0)) slow(c, cm, scs, wr, ch, fl);
         };
 
-        if constexpr (Cf::GPT == 2) {
-          // both of this warp's chunks in one load round trip, screened down
-          // to per-range maxima, scores and flags; the rare exact pass reads
-          // a flagged range's 8 correlations from tensor memory again, so no
-          // correlation stays in registers past the screen, and the
-          // accumulator goes back to the MMA after it (each tile set has two
-          // accumulators, so the MMA fills the other one meanwhile)
-          constexpr int R2 = 2 * RPC;
-          const int c0 = 2 * cp;
-          float cm[R2], scs[R2];
-          uint32_t fl = 0;
+        if constexpr (Cf::UNI) {
+          // this warp's chunks two at a time (one 64-column load each),
+          // screened down to the smallest margin score - threshold of the
+          // lane's ranges; nothing else stays in registers.  In the rare case
+          // that some lane passes, the exact pass reads each range's 8
+          // correlations from tensor memory again and recomputes its maximum
+          // and score (the same arithmetic, so the same values) against the
+          // current threshold (never looser than a valid bound); then the
+          // accumulator goes back to the MMA.
+          constexpr int CPW = Cf::NCH / Cf::GPT;  // chunks per warp
+          const int c0 = CPW * cp;
+          float m = INFINITY;
           if (ok) {
-            uint32_t ra[32], rb[32];
-            ptx::tmem_ld64_wait(tb + c0 * 32, ra, rb);
-            const float4 wa = *(const float4*)(sW + 4 * c0), wb = *(const float4*)(sW + 4 * c0 + 4);
-            const float4 ta = *(const float4*)(sThr + 4 * c0), tb4 = *(const float4*)(sThr + 4 * c0 + 4);
-            const float wv[R2] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-            const float tv[R2] = {ta.x, ta.y, ta.z, ta.w, tb4.x, tb4.y, tb4.z, tb4.w};
 #pragma unroll
-            for (int j = 0; j < R2; ++j) {
-              float v[8];
+            for (int h2 = 0; h2 < CPW; h2 += 2) {
+              uint32_t ra[32], rb[32];
+              ptx::tmem_ld64_wait(tb + (c0 + h2) * 32, ra, rb);
+              const int rb0 = (c0 + h2) * RPC;  // first range of the pair of chunks
+              const float4 wa = *(const float4*)(sW + rb0), wb = *(const float4*)(sW + rb0 + 4);
+              const float4 ta = *(const float4*)(sThr + rb0), tq = *(const float4*)(sThr + rb0 + 4);
+              const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+              const float tv[8] = {ta.x, ta.y, ta.z, ta.w, tq.x, tq.y, tq.z, tq.w};
+              float cm[8];
 #pragma unroll
-              for (int u = 0; u < 8; ++u)
-                v[u] = __uint_as_float(j < RPC ? ra[8 * j + u] : rb[8 * (j - RPC) + u]);
-              fl |= screen(v, wv[j], tv[j], cm[j], scs[j]) << j;
+              for (int j = 0; j < 8; ++j) {
+                const float* v = (const float*)(j < RPC ? ra + 8 * j : rb + 8 * (j - RPC));
+                cm[j] = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
+                              ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
+              }
+              if constexpr (MODE == MODE_GRID) {
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                  const float sa = score(cm[j], wv[j]), sb = score(cm[j + 1], wv[j + 1]);
+                  m = ptx::fmin3(m, sa - tv[j], sb - tv[j + 1]);
+                }
+              } else {
+                // two ranges per packed FMA: y = cmax - w sum Ds', the
+                // scores F_t - p_t y and the margins (a float difference is
+                // <= 0 exactly when sc <= thr)
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                  const float2 y2 = __ffma2_rn(make_float2(nX, nX), make_float2(wv[j], wv[j + 1]),
+                                               make_float2(cm[j], cm[j + 1]));
+                  float2 s2 = __ffma2_rn(make_float2(-p0f, -p0f), y2, make_float2(F0, F0));
+                  if constexpr (MODE == MODE_M2) {
+                    const float2 s1 = __ffma2_rn(make_float2(-p1f, -p1f), y2, make_float2(F1, F1));
+                    s2 = make_float2(fminf(s2.x, s1.x), fminf(s2.y, s1.y));
+                  }
+                  const float2 d2 = __fadd2_rn(s2, make_float2(-tv[j], -tv[j + 1]));
+                  m = ptx::fmin3(m, d2.x, d2.y);
+                }
+              }
             }
           }
-          if (!dvalid) fl = 0;
-          if (__any_sync(0xffffffffu, fl != 0)) {
+          if (__any_sync(0xffffffffu, dvalid && m <= 0.f)) {
             const DomRec dr = sDom[dl];
 #pragma unroll 1
-            for (int j = 0; j < R2; ++j) {
-              const bool mine = (fl >> j) & 1u;
-              if (!__any_sync(0xffffffffu, mine)) continue;
+            for (int j = 0; j < CPW * RPC; ++j) {
               const int r = c0 * RPC + j;
-              // (selects, not indexing: the arrays stay in registers)
-              float cmj = cm[0], scj = scs[0];
-#pragma unroll
-              for (int u = 1; u < R2; ++u)
-                if (j == u) cmj = cm[u], scj = scs[u];
+              float v[8];
+              ptx::tmem_ld8_wait(tb + c0 * 32 + 8 * j, v);
+              const float cmj = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
+                                      ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
+              const float scj = score(cmj, sW[r]);
+              const bool mine = dvalid && scj <= sThr[r];
+              if (!__any_sync(0xffffffffu, mine)) continue;
               float mn = mine ? scj : INFINITY;
 #pragma unroll
               for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
               const float lim = __fadd_ru(mn, 2.0f * sDelta[r]);
               const bool need = mine && scj <= lim;
               const unsigned bal = __ballot_sync(0xffffffffu, need);
-              float v[8];
-              ptx::tmem_ld8_wait(tb + c0 * 32 + 8 * j, v);
               int64_t be = INT64_MAX, bk = INT64_MAX;
               if (need) pair_exact(v, cmj, sW[r], dr, be, bk);
               if (__popc(bal) == 1) {
