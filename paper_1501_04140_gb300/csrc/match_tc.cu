@@ -32,7 +32,10 @@
 //               B = 16) and each tile's per-domain scoring planes and exact
 //               records;
 //   warp 1      allocates tensor memory and issues the MMAs (one thread);
-//   warps 2-3   idle (they complete the control warpgroup);
+//               at B <= 8 warp 2 issues too, each the MMAs of one of the
+//               two tile sets (the tiles whose accumulators one pair of
+//               epilogue groups reads);
+//   warps 2-3   otherwise idle (they complete the control warpgroup);
 //   warps 4-    epilogue, EG groups of four warps (four at B <= 8, two at
 //               B = 16): each warp owns the 32 TMEM lanes = 32 domains of its
 //               quarter.  At B = 16 the groups take turns on the tiles; at
@@ -128,6 +131,9 @@ struct TcCfg {
   // group per tile.
   static constexpr int GPT = UNI ? 2 : 1;             // warp groups per tile
   static constexpr int TSETS = EG / GPT;              // tiles scored at once
+  // MMA issuers: at B <= 8 one per tile set (warps 1 and 2), so that the
+  // refill of one set's accumulators never waits behind the other set's
+  static constexpr int NMMA = UNI ? TSETS : 1;
   static_assert(GPT == 1 || (NCH == 2 * GPT && NKC == 1), "two chunks per warp");
   static constexpr int MRG_BYTES = Wp::EPI_WARPS * kTileRanges * 16;  // per-warp range bests
   static constexpr int SCR_BYTES = 3 * kTileRanges * 4;  // per range: w, delta, threshold
@@ -226,7 +232,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
     }
     for (int i = 0; i < Cf::NA; ++i) {
       ptx::mbar_init(&a_full[i], 1);
-      ptx::mbar_init(&a_empty[i], 1);
+      ptx::mbar_init(&a_empty[i], Cf::NMMA);  // a commit from every MMA issuer
     }
     for (int i = 0; i < Cf::NACC; ++i) {
       ptx::mbar_init(&acc_full[i], 1);
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       ptx::mbar_init(&d_full[i], 1);
       ptx::mbar_init(&d_empty[i], 4);
     }
-    ptx::mbar_init(done_bar, 1);
+    ptx::mbar_init(done_bar, Cf::NMMA);
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
@@ -316,11 +322,14 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
         for (uint32_t i = 0; i < Cf::ND; ++i)
           if (di > i) ptx::mbar_spin(&d_full[i], ((i + (di - 1 - i) / Cf::ND * Cf::ND) / Cf::ND) & 1);
     }
-  } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
+  } else if (warp >= 1 && warp <= Cf::NMMA) {
+    // ------------------------------------------------------------ MMA issuers
+    // issuer `set` takes the tiles ti = set mod NMMA (all of them at B = 16)
     if (lane == 0) {
       constexpr uint32_t IDESC = ptx::idesc_f16_f32(kTileDoms, kTileRows);
-      uint32_t si = 0, ai = 0, ti = 0;
+      constexpr int NMMA = Cf::NMMA;
+      const int set = warp - 1;
+      uint32_t ai = 0, tib = 0;
       bool ok = true;
       for (int64_t it = blockIdx.x; ok && it < items; it += gridDim.x) {
         const ItemGeo g = item_geo(a, it, CH);
@@ -330,7 +339,10 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           break;
         }
         const uint8_t* sR = sA + rb * Cf::A_BYTES;
-        for (int kt = 0; ok && kt < g.t1 - g.t0; ++kt) {
+        const int len = g.t1 - g.t0;
+        for (int kt = (int)((set + NMMA - tib % NMMA) % NMMA); ok && kt < len; kt += NMMA) {
+          const uint32_t ti = tib + kt;
+          uint32_t si = ti * Cf::NKC;  // stage fills run in tile order, NKC per tile
           const int ab = ti % Cf::NACC;
           const uint32_t pa = ((ti / Cf::NACC) & 1) ^ 1;
           // one stage per tile: the accumulator and the stage are usually
@@ -363,8 +375,8 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           }
           if (!ok) break;
           ptx::mma_commit(&acc_full[ab]);
-          ++ti;
         }
+        tib += len;
         ptx::mma_commit(&a_empty[rb]);
         ++ai;
       }
