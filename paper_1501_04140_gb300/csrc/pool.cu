@@ -472,10 +472,11 @@ __global__ void k_sel_bases(SelState* st, int n_images) {
 // the bins' atomics rarely collide.
 //
 // Candidates.  Pools of up to kSelCand keys are copied to shared memory
-// whole.  Pools of up to kSelSampleMax keys first sort an evenly strided
-// sample of kSelSample keys and take the sample keys lo, hi kSelMargin
-// sample ranks below and above the target's estimated sample rank; one pass
-// over the keys counts those below lo and gathers those in [lo, hi].  When
+// whole.  Pools of up to kSelSampleMax keys first take an evenly strided
+// sample of kSelSample keys and bracket the sample keys kSelMargin sample
+// ranks below and above the target's estimated sample rank by lo, hi (a
+// histogram of the sample over its range); one pass over the keys counts
+// those below lo and gathers those in [lo, hi].  When
 // the target rank falls among the gathered keys (it does unless the sample
 // misjudges it by more than the margin, about four standard deviations) the
 // radix passes run on them alone, starting from the count below lo; all keys
@@ -488,13 +489,31 @@ __global__ void k_sel_bases(SelState* st, int n_images) {
 constexpr int kSelFusedThreads = 1024;
 constexpr int64_t kSelFusedMax = (int64_t)1 << 20;
 constexpr int kSelCand = 12288;         // candidate keys (dynamic shared memory)
-constexpr int kSelSample = 1024;        // sample keys (dynamic shared memory)
+constexpr int kSelSample = 1024;        // sample keys
 constexpr int kSelMargin = 64;          // sample ranks on each side of the estimate
 constexpr int64_t kSelSampleMax = 81920;  // about 10300 candidates expected at most
-constexpr int kSelDynBytes = (kSelCand + kSelSample) * 8;
+constexpr int kSelDynBytes = (kSelCand + 128) * 8;  // candidates, then a scratch of 128 keys
 constexpr int kSelWBits = 12;
 constexpr int kSelWBins = 1 << kSelWBits;
 constexpr int kSelWPasses = 4;  // 48 >= 45 key bits
+// A candidate in shared memory carries, above its key (< 2^45), the warp of
+// the compaction whose run of positions it came from.
+constexpr int kSelTagShift = 56;
+constexpr int64_t kSelKeyMask = ((int64_t)1 << kSelTagShift) - 1;
+
+// Adds 1 to cnt[d] for each lane with d >= 0, one atomic per run of equal d
+// over adjacent lanes; lanes with nothing to add pass distinct negative
+// values.  All 32 lanes call it.
+__device__ inline void warp_run_count(int* cnt, int d, int lane) {
+  const int dp = __shfl_up_sync(0xffffffffu, d, 1);
+  const bool head = lane == 0 || d != dp;
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  if (head && d >= 0) {
+    const unsigned after = heads & ~((2u << lane) - 1u);  // run heads above this lane
+    const int end = after ? __ffs(after) - 1 : 32;
+    atomicAdd(&cnt[d], end - lane);
+  }
+}
 
 __global__ void __launch_bounds__(kSelFusedThreads)
 k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ off,
@@ -504,16 +523,20 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
   __shared__ uint32_t hist[kSelWBins];
   extern __shared__ int64_t sel_dyn[];
   int64_t* cand = sel_dyn;               // kSelCand keys
-  int64_t* samp = sel_dyn + kSelCand;    // kSelSample keys
+  int64_t* samp = sel_dyn + kSelCand;    // scratch: warp minima and maxima, the bracket
   __shared__ int n_cand;
   __shared__ unsigned long long n_below;
   __shared__ int sw[32];
   __shared__ int wtot[32];
   __shared__ SelState s_st;
+  // compaction runs: warp w of the block owns positions [w seg, (w + 1) seg)
+  const int64_t P0 = off[blockIdx.x + 1] - off[blockIdx.x];
+  const int64_t seg = ceil_div64(ceil_div64(P0, 32), 32) * 32;  // a multiple of 32
   const int im = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t o0 = off[im], P = off[im + 1] - o0;
   const int64_t* k = keys + o0;
+  wtot[lane] = 0;  // (every warp writes the same zeros)
   if (threadIdx.x == 0) {
     int keep_all;
     SelState z{};
@@ -527,57 +550,116 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
   __syncthreads();
   bool in_smem = false;
   if (P <= kSelCand) {  // the whole pool as candidates
-    for (int64_t g = threadIdx.x; g < P; g += blockDim.x) cand[g] = __ldg(k + g);
+    for (int64_t g = threadIdx.x; g < P; g += blockDim.x)
+      cand[g] = __ldg(k + g) | ((g / seg) << kSelTagShift);
     if (threadIdx.x == 0) n_cand = (int)P;
     in_smem = true;
   } else if (P <= kSelSampleMax) {
-    for (int j = threadIdx.x; j < kSelSample; j += blockDim.x)
-      samp[j] = __ldg(k + (int64_t)j * P / kSelSample);
+    // the sample's keys of ranks ts -/+ kSelMargin, to the resolution of
+    // 4096 bins over the sample's range: lo = the low edge of the bin that
+    // holds the first, hi = the high edge of the bin that holds the second
+    // (so lo <= that key, hi >= the other: the bracket only widens)
+    static_assert(kSelSample == kSelFusedThreads, "one sample key per thread");
+    const int64_t sk = __ldg(k + (int64_t)threadIdx.x * P / kSelSample);
+    int64_t mn = sk, mx = sk;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = min(mn, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)mn, o));
+      mx = max(mx, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)mx, o));
+    }
+    for (int i = threadIdx.x; i < kSelWBins; i += blockDim.x) hist[i] = 0;
+    if (lane == 0) {
+      samp[warp] = mn;
+      samp[32 + warp] = mx;
+    }
     __syncthreads();
-    // bitonic sort of the sample, ascending
-    for (int kk = 2; kk <= kSelSample; kk <<= 1)
-      for (int j = kk >> 1; j > 0; j >>= 1) {
-        for (int t = threadIdx.x; t < kSelSample / 2; t += blockDim.x) {
-          const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1)), ip = i + j;
-          const int64_t a = samp[i], b = samp[ip];
-          if ((a > b) == ((i & kk) == 0)) {
-            samp[i] = b;
-            samp[ip] = a;
-          }
-        }
-        __syncthreads();
+    if (warp == 0) {
+      mn = samp[lane];
+      mx = samp[32 + lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)mn, o));
+        mx = max(mx, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)mx, o));
       }
+      if (lane == 0) {
+        samp[66] = mn;
+        samp[67] = mx;
+      }
+    }
+    __syncthreads();
+    const int64_t kmin = samp[66], kmax = samp[67];
+    int sh = 0;
+    while (((kmax - kmin) >> sh) >= kSelWBins) ++sh;
+    atomicAdd(&hist[(sk - kmin) >> sh], 1u);
+    __syncthreads();
     const int64_t rank0 = s_st.rank;
     const int ts = (int)(rank0 * kSelSample / P);
-    const int64_t lo = ts - kSelMargin >= 0 ? samp[ts - kSelMargin] : INT64_MIN;
-    const int64_t hi = ts + kSelMargin < kSelSample ? samp[ts + kSelMargin] : INT64_MAX;
-    // (warp-uniform loop: the lanes of a warp append together)
+    const int rlo = ts - kSelMargin, rhi = ts + kSelMargin;
+    constexpr int SPT = kSelWBins / kSelFusedThreads;  // bins per thread
+    uint32_t c[SPT];
+    int csum = 0;
+#pragma unroll
+    for (int u = 0; u < SPT; ++u) {
+      c[u] = hist[threadIdx.x * SPT + u];
+      csum += (int)c[u];
+    }
+    int tot;
+    int before = block_excl_scan(csum, sw, &tot);
+    if (threadIdx.x == 0) {
+      samp[64] = INT64_MIN;
+      samp[65] = INT64_MAX;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < SPT; ++u) {
+      const int b = threadIdx.x * SPT + u;
+      if (rlo >= 0 && before <= rlo && rlo < before + (int)c[u]) samp[64] = kmin + ((int64_t)b << sh);
+      if (rhi < kSelSample && before <= rhi && rhi < before + (int)c[u])
+        samp[65] = kmin + ((int64_t)(b + 1) << sh) - 1;
+      before += (int)c[u];
+    }
+    __syncthreads();
+    const int64_t lo = samp[64], hi = samp[65];
+    // one pass over the warp's compaction run: its keys below lo counted,
+    // those in [lo, hi] appended (one atomic per warp and 256 keys) with the
+    // warp as their tag
     int below = 0;
     constexpr int U = 8;
-    for (int64_t gb = (int64_t)warp * 32; gb < P; gb += (int64_t)U * blockDim.x) {
+    const int64_t g0 = (int64_t)warp * seg, g1 = min(P, g0 + seg);
+    for (int64_t gb = g0; gb < g1; gb += U * 32) {  // (warp-uniform)
       int64_t kk[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int64_t g = gb + (int64_t)u * blockDim.x + lane;
-        kk[u] = g < P ? __ldg(k + g) : -1;
+        const int64_t g = gb + u * 32 + lane;
+        kk[u] = g < g1 ? __ldg(k + g) : -1;
       }
+      unsigned m[U];
+      int n = 0;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const bool in = kk[u] >= 0 && kk[u] >= lo && kk[u] <= hi;  // (-1: past the end)
         below += kk[u] >= 0 && kk[u] < lo;
-        const unsigned m = __ballot_sync(0xffffffffu, in);
-        if (m) {
-          int b0 = 0;
-          if (lane == 0) b0 = atomicAdd(&n_cand, __popc(m));
-          b0 = __shfl_sync(0xffffffffu, b0, 0);
-          const int i = b0 + __popc(m & ((1u << lane) - 1u));
-          if (in && i < kSelCand) cand[i] = kk[u];
+        m[u] = __ballot_sync(0xffffffffu, in);
+        n += __popc(m[u]);
+      }
+      if (n) {
+        int b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&n_cand, n);
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = b0 + __popc(m[u] & ((1u << lane) - 1u));
+          if (((m[u] >> lane) & 1u) && i < kSelCand) cand[i] = kk[u] | ((int64_t)warp << kSelTagShift);
+          b0 += __popc(m[u]);
         }
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
-    if (lane == 0) atomicAdd(&n_below, (unsigned long long)below);
+    if (lane == 0) {
+      wtot[warp] = below;  // the warp's kept keys so far: all those below lo
+      atomicAdd(&n_below, (unsigned long long)below);
+    }
     __syncthreads();
     const int64_t nb = (int64_t)n_below, nc = n_cand;
     in_smem = nc <= kSelCand && nb <= rank0 && rank0 < nb + nc;  // uniform
@@ -591,6 +673,9 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
       }
     }
   }
+  // candidates that carry their compaction warp: the warps' kept counts come
+  // from shared memory, without a counting sweep over the keys
+  const bool tagged = in_smem;
   constexpr int BPT = kSelWBins / kSelFusedThreads;  // bins per thread in the scan
   for (int pass = 0; pass < kSelWPasses; ++pass) {
     const int shift = (kSelWPasses - 1 - pass) * kSelWBits;
@@ -602,7 +687,7 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
     if (in_smem) {
       const int nc = n_cand;
       for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-        const int64_t kk = cand[i];
+        const int64_t kk = cand[i] & kSelKeyMask;
         if ((kk >> (shift + kSelWBits)) == prefix)
           atomicAdd(&hist[(kk >> shift) & (kSelWBins - 1)], 1u);
       }
@@ -663,22 +748,32 @@ k_select_compact(const int64_t* __restrict__ keys, const int64_t* __restrict__ o
   // stable compaction: kept = key below the threshold (or equal, fallback)
   const int64_t thr = s_st.thr;
   const bool fb = s_st.fallback != 0;
-  const int64_t seg = ceil_div64(ceil_div64(P, 32), 32) * 32;  // per warp, a multiple of 32
   const int64_t g0 = (int64_t)warp * seg, g1 = min(P, g0 + seg);
-  int cnt = 0;
-  for (int64_t gb = g0; gb < g1; gb += 8 * 32) {
-    int64_t kk[8];
+  if (tagged) {  // the kept candidates of each warp's run, on top of its keys below lo
+    const int nc = n_cand;
+    for (int ib = warp * 32; ib < nc; ib += blockDim.x) {  // (warp-uniform)
+      const int i = ib + lane;
+      const int64_t c = i < nc ? cand[i] : -1;
+      const int64_t kk = c & kSelKeyMask;
+      const bool f = c >= 0 && (fb ? (kk <= thr) : (kk < thr));
+      warp_run_count(wtot, f ? (int)(c >> kSelTagShift) : -1 - lane, lane);
+    }
+  } else {
+    int cnt = 0;
+    for (int64_t gb = g0; gb < g1; gb += 8 * 32) {
+      int64_t kk[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int64_t g = gb + u * 32 + lane;
-      kk[u] = g < g1 ? __ldg(k + g) : -1;
+      for (int u = 0; u < 8; ++u) {
+        const int64_t g = gb + u * 32 + lane;
+        kk[u] = g < g1 ? __ldg(k + g) : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) cnt += kk[u] >= 0 && (fb ? (kk[u] <= thr) : (kk[u] < thr));
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) cnt += kk[u] >= 0 && (fb ? (kk[u] <= thr) : (kk[u] < thr));
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) wtot[warp] = cnt;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if (lane == 0) wtot[warp] = cnt;
   __syncthreads();
   int base = 0;
   for (int w2 = 0; w2 < warp; ++w2) base += wtot[w2];
@@ -762,8 +857,9 @@ __device__ inline int64_t bpack_index(int64_t slot, int e) {
 
 // One thread per (kept domain, 8-element K group): the group's 8 downsampled
 // values Ds - 512 (each the sum of a 2x2 pixel block, read as two pixel
-// pairs) go out as one 16-byte store of f16; the group-0 thread also writes
-// the domain's records.
+// pairs) go out as one 16-byte store of f16 (at B = 16 the warp of a domain
+// reads row by row instead, see below); the group-0 thread also writes the
+// domain's records.
 constexpr int kPackThreads = 256;
 
 template <int B>
@@ -793,12 +889,34 @@ k_pack_domains(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
     const int x0 = (pos % I.px) * L, y0 = (pos / I.px) * L;
     // pixel pairs as 2-byte loads where every pair starts on an even address
     const bool pairs = ((((uintptr_t)I.pix) | (uintptr_t)I.pitch | (uintptr_t)x0) & 1) == 0;
+    uint8_t* tile_blk = bpack ? (uint8_t*)bpack + (slot >> 7) * (int64_t)tc_tile_bytes(B) : nullptr;
+    if constexpr (B == 16) {
+      // a warp per domain (NG = 32): lane g takes cell column cj = g % 16 of
+      // every other cell row, so that each load of a half-warp reads 32
+      // consecutive pixels of one image row; one f16 store per cell
+      const int cj = g & 15;
+#pragma unroll 2
+      for (int ci = g >> 4; ci < B; ci += 2) {
+        const uint8_t* p = I.pix + (int64_t)(y0 + 2 * ci) * I.pitch + (x0 + 2 * cj);
+        int ds;
+        if (pairs) {
+          const uchar2 a = *(const uchar2*)p;
+          const uchar2 b = *(const uchar2*)(p + I.pitch);
+          ds = a.x + a.y + b.x + b.y;
+        } else {
+          ds = p[0] + p[1] + p[I.pitch] + p[I.pitch + 1];
+        }
+        const int e = ci * B + cj;
+        if (bpack) ((uint16_t*)tile_blk)[bpack_index<B>(slot & 127, e)] = f16_bits(ds - 512);
+        if (b32) b32[slot * n + e] = (float)(ds - 512);
+      }
+    }
     int v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int e = 8 * g + u;
       v[u] = 0;  // K padding (B = 2: K = 4 of 16)
-      if (e < n) {
+      if (B < 16 && e < n) {
         const int ci = e / B, cj = e % B;
         const uint8_t* p = I.pix + (int64_t)(y0 + 2 * ci) * I.pitch + (x0 + 2 * cj);
         int ds;
@@ -812,8 +930,7 @@ k_pack_domains(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
         v[u] = ds - 512;
       }
     }
-    uint8_t* tile_blk = bpack ? (uint8_t*)bpack + (slot >> 7) * (int64_t)tc_tile_bytes(B) : nullptr;
-    if (bpack) {
+    if (B < 16 && bpack) {
       uint4 q;
       q.x = f16_bits(v[0]) | ((uint32_t)f16_bits(v[1]) << 16);
       q.y = f16_bits(v[2]) | ((uint32_t)f16_bits(v[3]) << 16);
@@ -821,7 +938,7 @@ k_pack_domains(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
       q.w = f16_bits(v[6]) | ((uint32_t)f16_bits(v[7]) << 16);
       *(uint4*)((uint16_t*)tile_blk + bpack_index<B>(slot & 127, 8 * g)) = q;
     }
-    if (b32) {
+    if (B < 16 && b32) {
 #pragma unroll
       for (int u = 0; u < 8; ++u)
         if (8 * g + u < n) b32[slot * n + 8 * g + u] = (float)v[u];
