@@ -130,7 +130,7 @@ def _sm_max_mhz():
 # launch per level B on this workload, from one ncu capture of the current
 # kernel (cold caches: the operands' first touch); empty when the kernel has
 # changed since the last capture.
-TRAFFIC = {16: 20142848, 8: 6317056, 4: 3386368, 2: 3078912}
+TRAFFIC = {16: 20126720, 8: 6291200, 4: 3356416, 2: 3049216}
 
 
 def _dist():
