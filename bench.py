@@ -262,6 +262,47 @@ def run_tables(args):
     return 0
 
 
+# ------------------------------------------------------------------ decode
+def run_decode(args):
+    """Decoder throughput: the 512x512 headline image's saved maps decoded
+    from a flat 128 image to the fixed point (FP64 Jacobi steps until max
+    |delta| < 1e-7, then rounding) into device memory, timed with CUDA events
+    per decode; reports decoded images/s and pixel-iterations/s."""
+    import torch
+    from paper_1501_04140_gb300 import build, fic
+    build.build()
+    import oracle
+    from paper_1501_04140_gb300.synth import synth_image
+    ctx = fic.Context(0)
+    img = synth_image(512, 512, 1, n_textured=1)
+    d = torch.from_numpy(img).cuda()
+    code = ctx.encode(d, fic.default_params())
+    out = torch.zeros((512, 512), dtype=torch.uint8, device="cuda")
+    times, iters = [], 0
+    for s_ in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        code.decode(0, out=out)
+        e1.record()
+        e1.synchronize()
+        iters = code.iters
+        if s_ >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    psnr = oracle.psnr(img, out.cpu().numpy())
+    line = {"metric": "decoded images/s (512x512, to the fixed point)", "value": 1e3 / ms,
+            "unit": "images/s", "higher_is_better": True, "ms_per_decode": ms,
+            "iterations": iters, "pixel_iterations_per_s": 512 * 512 * iters / (ms * 1e-3),
+            "n_maps": code.count(0), "psnr_db": psnr, "steps": args.steps,
+            "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": "decode of the 512x512 encode (seed 1, one textured quadrant)"}}
+    code.free()
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -471,8 +512,8 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the library's default schedule (by default the library times "
                          "its schedules on the first encode and keeps the fastest)")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["tables"], default="512",
-                    help="512 (the headline), batch64, 4096 or tables (informational runs)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["tables", "decode"], default="512",
+                    help="512 (the headline), batch64, 4096, tables or decode (informational runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -480,6 +521,8 @@ def main():
         return run_reference(args)
     if args.workload == "tables":
         return run_tables(args)
+    if args.workload == "decode":
+        return run_decode(args)
     return run_ours(args)
 
 

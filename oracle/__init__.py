@@ -22,6 +22,7 @@ _lib = None
 
 S_PREDEFINED = 0
 S_GRID = 1
+S_EXACT = 2
 
 
 def build(force: bool = False) -> str:
@@ -53,7 +54,8 @@ class Code(C.Structure):
                 ("dom_index", C.c_int32), ("dom_x", C.c_int32), ("dom_y", C.c_int32),
                 ("iso", C.c_int32), ("s_idx", C.c_int32), ("p", C.c_int32), ("q", C.c_int32),
                 ("pad", C.c_int32), ("e_num", C.c_int64), ("o_num", C.c_int64),
-                ("e", C.c_double), ("s", C.c_double), ("o", C.c_double)]
+                ("e", C.c_double), ("s", C.c_double), ("o", C.c_double),
+                ("s_num", C.c_int64), ("s_den", C.c_int64)]
 
 
 class MatchResult(C.Structure):
@@ -70,9 +72,12 @@ class LevelStats(C.Structure):
 CODE_DTYPE = np.dtype([(n, "<i4") for n in ("level", "x", "y", "size", "dom_index", "dom_x",
                                              "dom_y", "iso", "s_idx", "p", "q", "pad")]
                       + [("e_num", "<i8"), ("o_num", "<i8"), ("e", "<f8"), ("s", "<f8"),
-                         ("o", "<f8")])
+                         ("o", "<f8"), ("s_num", "<i8"), ("s_den", "<i8")])
 MATCH_DTYPE = np.dtype([("e_num", "<i8"), ("key", "<i8"), ("dom_index", "<i4"),
                         ("iso", "<i4"), ("s_idx", "<i4"), ("pad", "<i4")])
+MATCH_EXACT_DTYPE = np.dtype([("key", "<i8"), ("s_num", "<i8"), ("s_den", "<i8"),
+                              ("dom_index", "<i4"), ("iso", "<i4"), ("e", "<f8"),
+                              ("e_lo", "<u8"), ("e_hi", "<u8")])
 
 _P = C.c_void_p
 
@@ -114,6 +119,15 @@ def lib():
             L.oracle_decode.argtypes = [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, _P]
             L.oracle_quantize_o.restype = None
             L.oracle_quantize_o.argtypes = [_P, C.c_int, C.c_int]
+            L.oracle_error_num128.restype = None
+            L.oracle_error_num128.argtypes = [_P, _P, C.c_int, C.c_int64, C.c_int64, _P]
+            L.oracle_s_exact.restype = None
+            L.oracle_s_exact.argtypes = [_P, _P, C.c_int, _P, _P]
+            L.oracle_mul_u128.restype = None
+            L.oracle_mul_u128.argtypes = [C.c_uint64] * 4 + [_P]
+            L.oracle_match_exact.restype = None
+            L.oracle_match_exact.argtypes = [_P, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int,
+                                             _P, C.c_int, _P, C.c_int, C.c_int, _P]
             L.oracle_code_bits.restype = C.c_int64
             L.oracle_code_bits.argtypes = [_P, C.c_int, _P, C.c_int]
             _lib = L
@@ -193,6 +207,43 @@ def error_direct(R, Ds, p, q):
     r = np.ascontiguousarray(R, dtype=np.int64).ravel()
     d = np.ascontiguousarray(Ds, dtype=np.int64).ravel()
     return float(lib().oracle_error_direct(_ptr(r), _ptr(d), r.size, p, q))
+
+
+def error_num128(R, Ds, p, q):
+    """16 q^2 n^2 E of Eq. 1 for 64-bit p, q, as a Python integer."""
+    r = np.ascontiguousarray(R, dtype=np.int64).ravel()
+    d = np.ascontiguousarray(Ds, dtype=np.int64).ravel()
+    out = np.zeros(2, np.uint64)
+    lib().oracle_error_num128(_ptr(r), _ptr(d), r.size, int(p), int(q), _ptr(out))
+    return int(out[0]) | (int(out[1]) << 64)
+
+
+def s_exact(R, Ds):
+    """Eq. 2's s of the pair, clamped to [0, 1], as (s_num, s_den)."""
+    r = np.ascontiguousarray(R, dtype=np.int64).ravel()
+    d = np.ascontiguousarray(Ds, dtype=np.int64).ravel()
+    sn, sd = C.c_int64(), C.c_int64()
+    lib().oracle_s_exact(_ptr(r), _ptr(d), r.size, C.byref(sn), C.byref(sd))
+    return int(sn.value), int(sd.value)
+
+
+def mul_u128(a, b):
+    """a * b of two unsigned 128-bit integers, through the oracle's limbs."""
+    out = np.zeros(4, np.uint64)
+    m = (1 << 64) - 1
+    lib().oracle_mul_u128(a & m, a >> 64, b & m, b >> 64, _ptr(out))
+    return sum(int(out[i]) << (64 * i) for i in range(4))
+
+
+def match_exact(img, B, L, kept, range_xy, n_threads=1):
+    a = _u8(img)
+    H, W = a.shape
+    kept = np.ascontiguousarray(kept, dtype=np.int32)
+    rxy = np.ascontiguousarray(range_xy, dtype=np.int32).reshape(-1, 2)
+    out = np.zeros(max(len(rxy), 1), MATCH_EXACT_DTYPE)
+    lib().oracle_match_exact(_ptr(a), W, W, H, B, L, _ptr(kept), len(kept), _ptr(rxy), len(rxy),
+                             n_threads, _ptr(out))
+    return out[:len(rxy)]
 
 
 def s_set(s_mode, grid_samples, B):

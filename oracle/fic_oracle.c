@@ -219,6 +219,76 @@ int64_t oracle_error_num(const int64_t* R, const int64_t* Ds, int n, int p, int 
   return (int64_t)acc;
 }
 
+void oracle_error_num128(const int64_t* R, const int64_t* Ds, int n, int64_t p, int64_t q,
+                         uint64_t* out) {
+  int64_t Sr = 0, Sd = 0;
+  for (int i = 0; i < n; ++i) {
+    Sr += R[i];
+    Sd += Ds[i];
+  }
+  /* each term is 4 q n times a residual of magnitude <= 510: below 2^57 for
+   * q <= 2^37 and n <= 256, so the sum of n squares stays below 2^128 */
+  unsigned __int128 acc = 0;
+  for (int i = 0; i < n; ++i) {
+    int64_t t = p * n * Ds[i] + 4 * q * Sr - p * Sd - 4 * q * n * R[i];
+    unsigned __int128 a = (unsigned __int128)(t < 0 ? -t : t);
+    acc += a * a;
+  }
+  out[0] = (uint64_t)acc;
+  out[1] = (uint64_t)(acc >> 64);
+}
+
+/* Eq. 2 with d = Ds / 4:
+ *   s = (n sum r d - sum r sum d) / (n sum d^2 - (sum d)^2)
+ *     = 4 (n sum r Ds - sum r sum Ds) / (n sum Ds^2 - (sum Ds)^2). */
+void oracle_s_exact(const int64_t* R, const int64_t* Ds, int n, int64_t* s_num, int64_t* s_den) {
+  int64_t Sr = 0, Sd = 0, Srd = 0, Sdd = 0;
+  for (int i = 0; i < n; ++i) {
+    Sr += R[i];
+    Sd += Ds[i];
+    Srd += R[i] * Ds[i];
+    Sdd += Ds[i] * Ds[i];
+  }
+  const int64_t C = (int64_t)n * Srd - Sr * Sd;
+  const int64_t V = (int64_t)n * Sdd - Sd * Sd;
+  if (V <= 0 || C <= 0) { /* flat block, or the best s in [0, 1] is 0 */
+    *s_num = 0;
+    *s_den = 1;
+  } else if (4 * C >= V) { /* s >= 1: clamped */
+    *s_num = 1;
+    *s_den = 1;
+  } else {
+    *s_num = 4 * C;
+    *s_den = V;
+  }
+}
+
+void oracle_mul_u128(uint64_t a_lo, uint64_t a_hi, uint64_t b_lo, uint64_t b_hi, uint64_t* out) {
+  const unsigned __int128 p00 = (unsigned __int128)a_lo * b_lo;
+  const unsigned __int128 p01 = (unsigned __int128)a_lo * b_hi;
+  const unsigned __int128 p10 = (unsigned __int128)a_hi * b_lo;
+  const unsigned __int128 p11 = (unsigned __int128)a_hi * b_hi;
+  const unsigned __int128 mid = (p00 >> 64) + (uint64_t)p01 + (uint64_t)p10;
+  const unsigned __int128 hi = (mid >> 64) + (p01 >> 64) + (p10 >> 64) + (uint64_t)p11;
+  out[0] = (uint64_t)p00;
+  out[1] = (uint64_t)mid;
+  out[2] = (uint64_t)hi;
+  out[3] = (uint64_t)(hi >> 64) + (uint64_t)(p11 >> 64);
+}
+
+/* sign of a_num / a_den^2 - b_num / b_den^2 (all non-negative, den > 0) */
+static int cmp_ratio(unsigned __int128 a_num, int64_t a_den, unsigned __int128 b_num,
+                     int64_t b_den) {
+  const unsigned __int128 a2 = (unsigned __int128)a_den * (unsigned __int128)a_den;
+  const unsigned __int128 b2 = (unsigned __int128)b_den * (unsigned __int128)b_den;
+  uint64_t x[4], y[4];
+  oracle_mul_u128((uint64_t)a_num, (uint64_t)(a_num >> 64), (uint64_t)b2, (uint64_t)(b2 >> 64), x);
+  oracle_mul_u128((uint64_t)b_num, (uint64_t)(b_num >> 64), (uint64_t)a2, (uint64_t)(a2 >> 64), y);
+  for (int i = 3; i >= 0; --i)
+    if (x[i] != y[i]) return x[i] < y[i] ? -1 : 1;
+  return 0;
+}
+
 double oracle_error_direct(const int64_t* R, const int64_t* Ds, int n, int p, int q) {
   long double s = (long double)p / (long double)q;
   long double rbar = 0.0L, dbar = 0.0L;
@@ -312,6 +382,83 @@ void oracle_match(const uint8_t* img, long pitch, int W, int H, int B, int L,
   free(Dall);
 }
 
+void oracle_match_exact(const uint8_t* img, long pitch, int W, int H, int B, int L,
+                        const int32_t* kept, int n_kept, const int32_t* range_xy, int n_ranges,
+                        int n_threads, oracle_match_exact_result* out) {
+  int nx, ny;
+  oracle_pool_size(W, H, B, L, &nx, &ny);
+  const int n = B * B;
+  int64_t* Dall = (int64_t*)malloc(sizeof(int64_t) * (size_t)n * (size_t)(n_kept > 0 ? n_kept : 1));
+  for (int j = 0; j < n_kept; ++j) {
+    int d = kept[j];
+    oracle_decimate(img, pitch, (d % nx) * L, (d / nx) * L, B, Dall + (size_t)j * n);
+  }
+  if (n_threads < 1) n_threads = 1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+#endif
+  for (int r = 0; r < n_ranges; ++r) {
+    int64_t R[256], T[256];
+    int rx = range_xy[2 * r], ry = range_xy[2 * r + 1];
+    for (int i = 0; i < B; ++i)
+      for (int jj = 0; jj < B; ++jj) R[i * B + jj] = img[(long)(ry + i) * pitch + rx + jj];
+    oracle_match_exact_result best;
+    memset(&best, 0, sizeof(best));
+    best.key = INT64_MAX;
+    best.dom_index = -1;
+    best.iso = -1;
+    unsigned __int128 best_num = 0;
+    for (int j = 0; j < n_kept; ++j) {
+      const int64_t* Ds = Dall + (size_t)j * n;
+      for (int k = 0; k < 8; ++k) {
+        oracle_isometry(Ds, B, k, T);
+        int64_t sn, sd;
+        oracle_s_exact(R, T, n, &sn, &sd);      /* Eq. 2 */
+        uint64_t e2[2];
+        oracle_error_num128(R, T, n, sn, sd, e2); /* Eq. 1 with Eq. 3's o */
+        const unsigned __int128 num = ((unsigned __int128)e2[1] << 64) | e2[0];
+        /* candidates arrive in increasing key order: strictly smaller E wins */
+        if (best.dom_index < 0 || cmp_ratio(num, sd, best_num, best.s_den) < 0) {
+          best_num = num;
+          best.key = (int64_t)kept[j] * 8 + k;
+          best.s_num = sn;
+          best.s_den = sd;
+          best.dom_index = kept[j];
+          best.iso = k;
+          best.e_lo = e2[0];
+          best.e_hi = e2[1];
+        }
+      }
+    }
+    out[r] = best;
+  }
+  free(Dall);
+}
+
+/* E in the moment form n E = A - G of the exact-s search, as the encoder
+ * reports it: with A = n sum r^2 - (sum r)^2 and the pair's C, V,
+ *   s = 0: A / n;   s = 1: (16 A - 8 C + V) / (16 n);   else (A - C C / V) / n,
+ * each operation in double in this order (the same value as Eq. 1's E up to
+ * rounding; the tests bound the difference). */
+static double exact_s_error(const int64_t* R, const int64_t* Ds, int n, int64_t s_num,
+                            int64_t s_den) {
+  int64_t Sr = 0, Srr = 0, Sd = 0, Srd = 0, Sdd = 0;
+  for (int i = 0; i < n; ++i) {
+    Sr += R[i];
+    Srr += R[i] * R[i];
+    Sd += Ds[i];
+    Srd += R[i] * Ds[i];
+    Sdd += Ds[i] * Ds[i];
+  }
+  const int64_t A = (int64_t)n * Srr - Sr * Sr;
+  const int64_t C = (int64_t)n * Srd - Sr * Sd;
+  const int64_t V = (int64_t)n * Sdd - Sd * Sd;
+  if (s_num == 0) return (double)A / (double)n;
+  if (s_num == s_den) return (double)(16 * A - 8 * C + V) / (16.0 * (double)n);
+  const double g = ((double)C * (double)C) / (double)V;
+  return ((double)A - g) / (double)n;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Quadtree encoder (Sec. 2) and decoder                                     */
 /* ------------------------------------------------------------------------ */
@@ -347,12 +494,29 @@ int oracle_encode(const uint8_t* img, long pitch, int W, int H, const oracle_par
     int fb;
     int n_kept = oracle_pool_filter(img, pitch, W, H, B, L, prm->entropy_percentile,
                                     prm->pool_size, keys, kept, &thr, &fb);
-    int32_t sp[64], q;
-    int n_s = oracle_s_set(prm->s_mode, prm->grid_samples, B, sp, &q);
+    int32_t sp[64], q = 1;
+    const int exact = prm->s_mode == ORACLE_S_EXACT;
+    int n_s = exact ? 1 : oracle_s_set(prm->s_mode, prm->grid_samples, B, sp, &q);
     oracle_match_result* res =
         (oracle_match_result*)malloc(sizeof(oracle_match_result) * (size_t)(n_active > 0 ? n_active : 1));
-    oracle_match(img, pitch, W, H, B, L, kept, n_kept, active, n_active, sp, n_s, q,
-                 prm->n_threads, res);
+    oracle_match_exact_result* rex = NULL;
+    if (exact) {
+      rex = (oracle_match_exact_result*)malloc(sizeof(oracle_match_exact_result) *
+                                               (size_t)(n_active > 0 ? n_active : 1));
+      oracle_match_exact(img, pitch, W, H, B, L, kept, n_kept, active, n_active, prm->n_threads,
+                         rex);
+      for (int r = 0; r < n_active; ++r) {
+        res[r].e_num = 0;
+        res[r].key = rex[r].key;
+        res[r].dom_index = rex[r].dom_index;
+        res[r].iso = rex[r].iso;
+        res[r].s_idx = 0;
+        res[r].pad = 0;
+      }
+    } else {
+      oracle_match(img, pitch, W, H, B, L, kept, n_kept, active, n_active, sp, n_s, q,
+                   prm->n_threads, res);
+    }
 
     const int last = (lv == n_lv - 1) || prm->single_level;
     const double den = 16.0 * q * q * (double)n * (double)n;
@@ -361,6 +525,16 @@ int oracle_encode(const uint8_t* img, long pitch, int W, int H, const oracle_par
     for (int r = 0; r < n_active; ++r) {
       int rx = active[2 * r], ry = active[2 * r + 1];
       double e = (double)res[r].e_num / den;
+      int64_t Rb[256], Tb[256];
+      if (exact) { /* E of the chosen pair in the moment form */
+        int d = res[r].dom_index;
+        int64_t Dd[256];
+        for (int i = 0; i < B; ++i)
+          for (int j = 0; j < B; ++j) Rb[i * B + j] = img[(long)(ry + i) * pitch + rx + j];
+        oracle_decimate(img, pitch, (d % nx) * L, (d / nx) * L, B, Dd);
+        oracle_isometry(Dd, B, res[r].iso, Tb);
+        e = exact_s_error(Rb, Tb, n, rex[r].s_num, rex[r].s_den);
+      }
       if (last || e <= e_thr) {
         n_acc++;
         if (n_codes >= cap) {
@@ -375,7 +549,7 @@ int oracle_encode(const uint8_t* img, long pitch, int W, int H, const oracle_par
           for (int j = 0; j < B; ++j) Sr += img[(long)(ry + i) * pitch + rx + j];
         oracle_decimate(img, pitch, (d % nx) * L, (d / nx) * L, B, Ds);
         for (int i = 0; i < n; ++i) Sd += Ds[i];
-        int p = sp[res[r].s_idx];
+        int p = exact ? 0 : sp[res[r].s_idx];
         c->level = lv;
         c->x = rx;
         c->y = ry;
@@ -385,14 +559,27 @@ int oracle_encode(const uint8_t* img, long pitch, int W, int H, const oracle_par
         c->dom_y = (d / nx) * L;
         c->iso = res[r].iso;
         c->s_idx = res[r].s_idx;
-        c->p = p;
-        c->q = q;
-        c->e_num = res[r].e_num;
         c->e = e;
-        c->s = (double)p / (double)q;
-        /* Eq. 3: o = Sr / n - (p / q) Sd / (4 n) = (4 q Sr - p Sd) / (4 q n) */
-        c->o_num = 4LL * q * Sr - (int64_t)p * Sd;
-        c->o = (double)c->o_num / (4.0 * q * (double)n);
+        if (exact) {
+          /* Eq. 3 with s = s_num / s_den: o = (4 s_den Sr - s_num Sd) / (4 s_den n) */
+          c->p = c->q = 0;
+          c->e_num = 0;
+          c->o_num = 0;
+          c->s_num = rex[r].s_num;
+          c->s_den = rex[r].s_den;
+          c->s = (double)c->s_num / (double)c->s_den;
+          c->o = (double)(4 * c->s_den * Sr - c->s_num * Sd) / (4.0 * (double)c->s_den * (double)n);
+        } else {
+          c->p = p;
+          c->q = q;
+          c->e_num = res[r].e_num;
+          c->s_num = p;
+          c->s_den = q;
+          c->s = (double)p / (double)q;
+          /* Eq. 3: o = Sr / n - (p / q) Sd / (4 n) = (4 q Sr - p Sd) / (4 q n) */
+          c->o_num = 4LL * q * Sr - (int64_t)p * Sd;
+          c->o = (double)c->o_num / (4.0 * q * (double)n);
+        }
       } else {
         int h = B / 2;
         int32_t* o = next + 2 * (size_t)n_next;
@@ -414,6 +601,7 @@ int oracle_encode(const uint8_t* img, long pitch, int W, int H, const oracle_par
       stats[lv].matches = (double)n_active * (double)n_kept * 8.0;
     }
     free(res);
+    free(rex);
     free(keys);
     free(kept);
     int32_t* t = active;
@@ -469,7 +657,7 @@ int oracle_decode(const oracle_code* codes, int n_codes, int W, int H, int max_i
     for (int c = 0; c < n_codes; ++c) {
       const oracle_code* k = &codes[c];
       const int B = k->size;
-      const double s = (double)k->p / (double)k->q;
+      const double s = k->s; /* p / q, or Eq. 2's s in the exact-s mode */
       for (int i = 0; i < B; ++i)
         for (int j = 0; j < B; ++j) {
           int si, sj;

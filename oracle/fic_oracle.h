@@ -27,6 +27,7 @@ extern "C" {
 /* S-set selection. */
 #define ORACLE_S_PREDEFINED 0 /* Sec. 3.1 per-step sets, denominators 10  */
 #define ORACLE_S_GRID 1       /* k/(M-1), k = 0..M-1 (Sec. 2 "pre-sampled") */
+#define ORACLE_S_EXACT 2      /* Eq. 2's s of every pair, clamped to [0, 1] */
 
 typedef struct {
   int n_levels;              /* 1..4 */
@@ -48,13 +49,17 @@ typedef struct {
   int32_t dom_index;           /* raster index in the unfiltered pool     */
   int32_t dom_x, dom_y;        /* domain block top-left corner (2B x 2B)  */
   int32_t iso;                 /* isometry 0..7                           */
-  int32_t s_idx, p, q;         /* s = p / q, s_idx its index in the set   */
+  int32_t s_idx, p, q;         /* s = p / q, s_idx its index in the set
+                                  (exact-s mode: s_idx = p = q = 0)       */
   int32_t pad;
-  int64_t e_num;               /* 16 q^2 n^2 E, exact                     */
-  int64_t o_num;               /* 4 q n o, exact                          */
-  double e;                    /* E = e_num / (16 q^2 n^2)                */
-  double s;                    /* p / q                                   */
-  double o;                    /* o_num / (4 q n)                         */
+  int64_t e_num;               /* 16 q^2 n^2 E, exact (exact-s mode: 0)   */
+  int64_t o_num;               /* 4 q n o, exact (exact-s mode: 0)        */
+  double e;                    /* E = e_num / (16 q^2 n^2); exact-s mode:
+                                  the moment form below                   */
+  double s;                    /* p / q (exact-s mode: s_num / s_den)     */
+  double o;                    /* o_num / (4 q n) (exact-s mode: with
+                                  s_num, s_den in place of p, q)          */
+  int64_t s_num, s_den;        /* s as an exact fraction (every mode)     */
 } oracle_code;
 
 typedef struct {
@@ -122,6 +127,33 @@ void oracle_match(const uint8_t* img, long pitch, int W, int H, int B, int L,
                   int n_ranges, const int32_t* s_p, int n_s, int q, int n_threads,
                   oracle_match_result* out);
 
+/* 16 q^2 n^2 E of Eq. 1 as oracle_error_num, for 64-bit p and q and as an
+ * unsigned 128-bit integer (out[0] = low, out[1] = high 64 bits). */
+void oracle_error_num128(const int64_t* R, const int64_t* Ds, int n, int64_t p, int64_t q,
+                         uint64_t* out);
+/* Eq. 2's least-squares s of a range R and a (transformed) decimated block
+ * d = Ds / 4: s = (n sum r d - sum r sum d) / (n sum d^2 - (sum d)^2), in
+ * integer moments 4C / V with C = n sum r Ds - sum r sum Ds and
+ * V = n sum Ds^2 - (sum Ds)^2.  Reading: s stays in [0, 1] (clamped), and a
+ * flat block (V = 0) takes s = 0.  Returned as *s_num / *s_den. */
+void oracle_s_exact(const int64_t* R, const int64_t* Ds, int n, int64_t* s_num, int64_t* s_den);
+/* a * b of two unsigned 128-bit integers as four 64-bit limbs, low first
+ * (the products of the exact-s comparisons). */
+void oracle_mul_u128(uint64_t a_lo, uint64_t a_hi, uint64_t b_lo, uint64_t b_hi, uint64_t* out);
+typedef struct {
+  int64_t key;                 /* dom_index * 8 + iso                     */
+  int64_t s_num, s_den;        /* the pair's s (oracle_s_exact)           */
+  int32_t dom_index, iso;
+  double e;                    /* E, the moment form (oracle_encode)      */
+  uint64_t e_lo, e_hi;         /* 16 s_den^2 n^2 E, exact (Eq. 1)         */
+} oracle_match_exact_result;
+/* The exact-s search: for each listed range, the (domain, isometry) whose
+ * Eq. 1 error at its own Eq. 2 s (oracle_s_exact) and Eq. 3 o is smallest,
+ * compared exactly (E_a < E_b iff num_a den_b^2 < num_b den_a^2, 256-bit
+ * products); ties go to the lowest key dom_index * 8 + iso. */
+void oracle_match_exact(const uint8_t* img, long pitch, int W, int H, int B, int L,
+                        const int32_t* kept, int n_kept, const int32_t* range_xy, int n_ranges,
+                        int n_threads, oracle_match_exact_result* out);
 /* Full quadtree encoder.  Returns the number of codes (or -1 if cap is too
  * small, -2 on bad arguments).  stats has n_levels entries. */
 int oracle_encode(const uint8_t* img, long pitch, int W, int H, const oracle_params* prm,

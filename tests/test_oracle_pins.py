@@ -355,6 +355,139 @@ def test_encode_equals_brute_force_quadtree():
     assert sum(s["n_accepted"] for s in stats) == len(codes)
 
 
+# ---------------------------------------------------------------- exact s (Eq. 2)
+
+def _eq1_min_over_unit_interval(R, Ds):
+    """min over s in [0, 1] of Eq. 1 (with Eq. 3's o) from Eq. 1 alone: E(s)
+    is a quadratic in s, fitted exactly through s = 0, 1/2, 1."""
+    e0 = _eq1_fraction(R, Ds, Fraction(0))
+    eh = _eq1_fraction(R, Ds, Fraction(1, 2))
+    e1 = _eq1_fraction(R, Ds, Fraction(1))
+    a = 2 * (e1 - 2 * eh + e0)          # E(s) = a s^2 + b s + c
+    b = e1 - e0 - a
+    if a == 0:
+        s = Fraction(0) if b >= 0 else Fraction(1)
+    else:
+        s = min(max(-b / (2 * a), Fraction(0)), Fraction(1))
+    return s, _eq1_fraction(R, Ds, s)
+
+
+def test_s_exact_minimises_eq1_on_unit_interval():
+    """oracle_s_exact's s is the minimiser of Eq. 1 over [0, 1] (found here
+    from Eq. 1 alone), including the clamped ends and the flat block."""
+    rng = np.random.default_rng(31)
+    cases = []
+    for B in (2, 4, 8, 16):
+        n = B * B
+        for _ in range(4):
+            cases.append((rng.integers(0, 256, size=n), rng.integers(0, 1021, size=n)))
+        base = rng.integers(0, 1021, size=n)
+        cases.append((255 - base // 4, base))                       # anti-correlated: s = 0
+        cases.append((np.clip(2 * (base // 4) - 100, 0, 255), base))  # slope 2: s = 1
+        cases.append((rng.integers(0, 256, size=n), np.full(n, 400)))   # flat: s = 0
+        cases.append((base // 8 + 30, base))                        # slope 1/2: s = 1/2
+    seen = set()
+    for R, Ds in cases:
+        sn, sd = oracle.s_exact(R, Ds)
+        s_or = Fraction(sn, sd)
+        s_bf, e_bf = _eq1_min_over_unit_interval(R, Ds)
+        assert _eq1_fraction(R, Ds, s_or) == e_bf
+        if e_bf > 0 and s_bf != s_or:  # several minimisers only when E is flat in s
+            assert _eq1_fraction(R, Ds, s_bf) == _eq1_fraction(R, Ds, s_or)
+        seen.add("0" if s_or == 0 else "1" if s_or == 1 else "mid")
+        # the oracle's 128-bit integer form of Eq. 1 at that s is exact
+        n = len(R)
+        assert Fraction(oracle.error_num128(R, Ds, sn, sd), 16 * sd * sd * n * n) == e_bf
+    assert seen == {"0", "1", "mid"}
+
+
+def test_mul_u128_matches_python_integers():
+    rng = np.random.default_rng(32)
+    for _ in range(200):
+        a = int(rng.integers(0, 1 << 62)) << int(rng.integers(0, 66))
+        b = int(rng.integers(0, 1 << 62)) << int(rng.integers(0, 66))
+        a &= (1 << 128) - 1
+        b &= (1 << 128) - 1
+        assert oracle.mul_u128(a, b) == a * b
+    top = (1 << 128) - 1
+    assert oracle.mul_u128(top, top) == top * top
+
+
+@pytest.mark.parametrize("B,L", [(2, 2), (4, 3), (8, 4)])
+def test_match_exact_equals_rational_brute_force(B, L):
+    """The exact-s search equals the exhaustive argmin over (domain,
+    isometry) of each pair's minimum of Eq. 1 over s in [0, 1] (found from
+    Eq. 1 alone), ties to the lowest key dom_index * 8 + k."""
+    img = synth_image(40, 40, 33, n_textured=1)
+    keys, kept, thr, fb = oracle.pool_filter(img, B, L, 0.5)
+    kept = kept[:10]
+    H, W = img.shape
+    nx = (W - 2 * B) // L + 1
+    ranges = [(x, y) for y in range(0, 40, B * 3) for x in range(0, 40, B * 2)][:8]
+    got = oracle.match_exact(img, B, L, kept, ranges)
+    n = B * B
+    for g, (rx, ry) in zip(got, ranges):
+        R = img[ry:ry + B, rx:rx + B].astype(np.int64)
+        best = None
+        for d in kept:
+            dx, dy = (d % nx) * L, (d // nx) * L
+            Ds = img[dy:dy + 2 * B, dx:dx + 2 * B].astype(np.int64).reshape(B, 2, B, 2).sum(axis=(1, 3))
+            for k in range(8):
+                T = np.rot90(Ds, k=-(k % 4))
+                if k >= 4:
+                    T = np.fliplr(T)
+                s_bf, e_bf = _eq1_min_over_unit_interval(R.ravel(), T.ravel())
+                key = int(d) * 8 + k
+                if best is None or (e_bf, key) < best:
+                    best = (e_bf, key)
+        e_or = Fraction(int(g["e_lo"]) | (int(g["e_hi"]) << 64), 16 * int(g["s_den"]) ** 2 * n * n)
+        assert (e_or, int(g["key"])) == best
+
+
+def test_encode_exact_s_ramp_is_exact_at_the_first_level():
+    """f(x, y) = x: with s free in [0, 1] the first level already finds
+    s = 1/2 and E = 0 for every 16 x 16 range (the predefined sets need the
+    2 x 2 level for that), and the decoder returns f."""
+    img = np.tile(np.arange(64, dtype=np.uint8), (64, 1))
+    codes, stats = oracle.encode(img, oracle.make_params(rms_threshold=0.0, s_mode=oracle.S_EXACT))
+    assert [st["n_accepted"] for st in stats] == [16, 0, 0, 0]
+    assert np.all(codes["e"] == 0.0)
+    assert np.all(codes["s"] == 0.5) and np.all(codes["s_num"] * 2 == codes["s_den"])
+    dec, it = oracle.decode(codes, 64, 64)
+    assert np.max(np.abs(dec - img)) < 1e-6
+
+
+def test_encode_exact_s_codes_follow_eq1_to_eq3():
+    """Every saved map of an exact-s encode: s is Eq. 2's value clamped to
+    [0, 1], o is Eq. 3 (both as doubles of the exact fractions) and the
+    reported E (moment form in double) is Eq. 1's exact error to 1e-12."""
+    img = synth_image(64, 64, 34, n_textured=1)
+    codes, stats = oracle.encode(img, oracle.make_params(s_mode=oracle.S_EXACT))
+    assert len(codes) > 20
+    for c in codes[::3]:
+        B = int(c["size"])
+        n = B * B
+        R = img[c["y"]:c["y"] + B, c["x"]:c["x"] + B].astype(np.int64)
+        Ds = img[c["dom_y"]:c["dom_y"] + 2 * B, c["dom_x"]:c["dom_x"] + 2 * B].astype(np.int64)
+        Ds = Ds.reshape(B, 2, B, 2).sum(axis=(1, 3))
+        k = int(c["iso"])
+        T = np.rot90(Ds, k=-(k % 4))
+        if k >= 4:
+            T = np.fliplr(T)
+        r = [Fraction(int(v)) for v in R.ravel()]
+        d = [Fraction(int(v), 4) for v in T.ravel()]
+        rb, db = sum(r) / n, sum(d) / n
+        vd = sum((x - db) ** 2 for x in d)
+        cov = sum((a - rb) * (x - db) for a, x in zip(r, d))
+        s_ls = cov / vd if vd else Fraction(0)       # Eq. 2
+        s_cl = min(max(s_ls, Fraction(0)), Fraction(1))
+        assert Fraction(int(c["s_num"]), int(c["s_den"])) == s_cl
+        assert c["s"] == float(s_cl)
+        assert c["o"] == pytest.approx(float(rb - s_cl * db), rel=1e-15, abs=1e-12)  # Eq. 3
+        e = _eq1_fraction(R.ravel(), T.ravel(), s_cl)
+        assert c["e"] == pytest.approx(float(e), rel=1e-12, abs=1e-9)
+
+
 def test_encode_flat_image_is_exact():
     img = np.full((64, 64), 173, np.uint8)
     codes, stats = oracle.encode(img, oracle.make_params(rms_threshold=0.0))
