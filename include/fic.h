@@ -56,6 +56,14 @@ extern "C" {
 /* contrast-scaling set (Sec. 2 grid search; Sec. 3.1 predefined values) */
 #define FIC_S_PREDEFINED 0 /* 16:{0.1} 8:{0.2,0.4} 4:{0.3,0.8} 2:{0.5,0.9} */
 #define FIC_S_GRID 1       /* s_k = k/(M-1), k = 0..M-1, 2 <= M <= 32      */
+#define FIC_S_EXACT 2      /* Eq. 2's least-squares s of every (range,
+                              domain, isometry), clamped to [0, 1] (a flat
+                              domain takes s = 0): the exhaustive search the
+                              paper derives its predefined values from
+                              (Sec. 3.1).  The best map minimises Eq. 1 at its
+                              own s, compared exactly; ties go to the lowest
+                              dom_index * 8 + iso.  Tensor precision only
+                              (FIC_EUNSUPPORTED with FIC_PREC_FP32).        */
 
 /* arithmetic of the correlation <R, D> */
 #define FIC_PREC_TENSOR 0 /* tcgen05 f16 MMA on exact small integers, exact
@@ -72,9 +80,9 @@ typedef struct {
   int range_size0;           /* B at the first level: 16, 8, 4 or 2            */
   int domain_step;           /* L >= 1 (Sec. 2)                                */
   double rms_threshold;      /* accept a range when E <= n T^2, compared as
-                                (double)e_num / (16 q^2 n^2) <= n (T T)        */
+                                e <= n (T T) with e the map's double E below  */
   int single_level;          /* 1: one level, every range accepted             */
-  int s_mode;                /* FIC_S_PREDEFINED or FIC_S_GRID                 */
+  int s_mode;                /* FIC_S_PREDEFINED, FIC_S_GRID or FIC_S_EXACT    */
   int grid_samples;          /* M for FIC_S_GRID                               */
   double entropy_percentile; /* threshold = pool entropy at this percentile    */
   int precision;             /* FIC_PREC_TENSOR or FIC_PREC_FP32               */
@@ -106,13 +114,22 @@ typedef struct {
   int32_t dom_x, dom_y;      /* domain top-left (a 2B x 2B square)            */
   int32_t iso;               /* 0..3: rotate 90k deg clockwise; 4..7: then
                                 mirror left-right                             */
-  int32_t s_idx, p, q;       /* s = p / q, s_idx its index in the level's set */
+  int32_t s_idx, p, q;       /* s = p / q, s_idx its index in the level's set
+                                (FIC_S_EXACT: s_idx = p = q = 0)              */
   int32_t reserved;
-  int64_t e_num;             /* 16 q^2 n^2 E, exact integer                   */
-  int64_t o_num;             /* 4 q n o, exact integer                        */
-  double e;                  /* E of Eq. 1                                    */
-  double s;                  /* p / q                                         */
-  double o;                  /* o of Eq. 3                                    */
+  int64_t e_num;             /* 16 q^2 n^2 E, exact integer (FIC_S_EXACT: 0)  */
+  int64_t o_num;             /* 4 q n o, exact integer (FIC_S_EXACT: 0)       */
+  double e;                  /* E of Eq. 1: e_num / (16 q^2 n^2); FIC_S_EXACT:
+                                with the pair's integer moments
+                                A = n sum r^2 - (sum r)^2, C = n <r, Ds> -
+                                sum r sum Ds, V = n sum Ds^2 - (sum Ds)^2 (Ds
+                                the 2x2 sums of the domain), in double in this
+                                order: s = 0: A / n; s = 1: (16A - 8C + V) /
+                                (16 n); otherwise (A - (C C) / V) / n          */
+  double s;                  /* p / q; FIC_S_EXACT: 4C / V (or 0, 1)          */
+  double o;                  /* o of Eq. 3: o_num / (4 q n); FIC_S_EXACT:
+                                (4 d sum r - m sum Ds) / ((4 d) n) for
+                                s = m / d, m = 4C, d = V (0/1, 1/1 clamped)    */
 } fic_transform;
 
 /* Per-range result of fic_match_level (same fields as fic_transform). */
@@ -234,7 +251,8 @@ int fic_code_stats(const fic_code* code, int image_idx, fic_level_stats* host_ou
  * (asynchronous on the code's last stream; later decodes use o').  e, e_num
  * and o_num keep the unquantised map's values.  fic_code_bits writes the
  * total bits of one image's stored form to *bits (synchronises); the
- * compression ratio is 8 W H / bits.  FIC_EINVAL for o_bits outside 1..16. */
+ * compression ratio is 8 W H / bits.  FIC_EINVAL for o_bits outside 1..16,
+ * and from fic_code_bits for FIC_S_EXACT codes (s is not from a finite set). */
 int fic_code_quantize_o(fic_code* code, int o_bits);
 int fic_code_bits(const fic_code* code, int image_idx, int o_bits, int64_t* bits);
 
@@ -276,7 +294,7 @@ int fic_decode(fic_ctx* ctx, const fic_code* code, int image_idx, int max_iters,
  *
  *   codes      n_codes maps in DEVICE memory, caller-owned (for example the
  *              output of fic_code_get copied to the device); every block must
- *              lie inside the image, sizes 2/4/8/16, iso 0..7, q > 0
+ *              lie inside the image, sizes 2/4/8/16, iso 0..7, 0 <= s <= 1
  *              (FIC_EINVAL otherwise, checked on the device before decoding)
  *   out        width x height bytes at out_pitch, DEVICE memory, caller-owned
  *   iters_done iterations run (may be NULL)

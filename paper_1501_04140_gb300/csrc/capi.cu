@@ -151,13 +151,16 @@ int check_params(const fic_params* p) {
   if (B0 != 2 && B0 != 4 && B0 != 8 && B0 != 16) return FIC_EINVAL;
   if (p->n_levels < 1 || p->n_levels > 4 || (B0 >> (p->n_levels - 1)) < 2) return FIC_EINVAL;
   if (p->domain_step < 1) return FIC_EINVAL;
-  if (p->s_mode != FIC_S_PREDEFINED && p->s_mode != FIC_S_GRID) return FIC_EINVAL;
+  if (p->s_mode != FIC_S_PREDEFINED && p->s_mode != FIC_S_GRID && p->s_mode != FIC_S_EXACT)
+    return FIC_EINVAL;
   if (p->s_mode == FIC_S_GRID && (p->grid_samples < 2 || p->grid_samples > kMaxS))
     return FIC_EINVAL;
   if (!(p->entropy_percentile >= 0.0 && p->entropy_percentile <= 1.0)) return FIC_EINVAL;
   if (p->precision != FIC_PREC_TENSOR && p->precision != FIC_PREC_FP32) return FIC_EINVAL;
   if (!(p->rms_threshold >= 0.0)) return FIC_EINVAL;
   if (p->pool_size < 0) return FIC_EINVAL;
+  // the exact-s search exists on the tensor path only
+  if (p->s_mode == FIC_S_EXACT && p->precision != FIC_PREC_TENSOR) return FIC_EUNSUPPORTED;
   return FIC_OK;
 }
 
@@ -367,6 +370,7 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
   a.item_off = w.item_off.as<int64_t>();
   a.chunks = w.chunks.as<int32_t>();
   a.meta = w.meta.as<PlanMeta>();
+  a.pm = PosMoments{pl.sd.as<int32_t>(), pl.sq.as<int32_t>(), pl.off.as<int64_t>()};
   a.part = w.part.as<Cand>();
   a.status = ctx->status.as<uint32_t>();
   auto match = [&]() { return tc ? launch_match_tc(a, grid, st) : launch_match_f32(a, grid, st); };
@@ -419,7 +423,7 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
                              w.meta.as<PlanMeta>(), ctx->status.as<uint32_t>(),
                              w.res.as<fic_transform>(), prm.rms_threshold, split > 0 ? 1 : 0,
                              split >= 0 ? w.acc.as<uint8_t>() : nullptr, w.acc_cnt.as<int32_t>(),
-                             w.rej_cnt.as<int32_t>(), st);
+                             w.rej_cnt.as<int32_t>(), a.pm, st);
 }
 
 int64_t ranges_at(const std::vector<fic_image>& ims, int B) {
@@ -643,7 +647,8 @@ int fic_destroy(fic_ctx* c) {
 // ------------------------------------------------------------ pools
 int fic_build_domain_pool(fic_ctx* ctx, const fic_image* img, int range_size,
                           const fic_params* params, void* stream, fic_pool** out) {
-  if (!ctx || !img || !out || check_params(params)) return FIC_EINVAL;
+  if (!ctx || !img || !out || !params) return FIC_EINVAL;
+  if (const int pc = check_params(params)) return pc;
   *out = nullptr;
   if (range_size != 2 && range_size != 4 && range_size != 8 && range_size != 16) return FIC_EINVAL;
   if (!valid_image(*img, range_size)) return FIC_EINVAL;
@@ -748,7 +753,8 @@ void fic_pool_free(fic_pool* p) {
 int fic_match_level(fic_ctx* ctx, const fic_image* img, const fic_pool* pool,
                     const int32_t* range_xy, int n_ranges, const fic_params* params, void* stream,
                     fic_matches** out) {
-  if (!ctx || !img || !pool || !out || check_params(params) || n_ranges < 0) return FIC_EINVAL;
+  if (!ctx || !img || !pool || !out || !params || n_ranges < 0) return FIC_EINVAL;
+  if (const int pc = check_params(params)) return pc;
   if (n_ranges > 0 && !range_xy) return FIC_EINVAL;
   *out = nullptr;
   const int B = pool->pl.B;
@@ -873,8 +879,9 @@ static bool code_compatible(const fic_code* c, const fic_image* imgs, int n_imag
 
 int fic_encode(fic_ctx* ctx, const fic_image* imgs, int n_images, const fic_params* params,
                void* stream, fic_code** out) {
-  if (!ctx || !imgs || !out || n_images < 1 || n_images > kMaxImages || check_params(params))
+  if (!ctx || !imgs || !out || n_images < 1 || n_images > kMaxImages || !params)
     return FIC_EINVAL;
+  if (const int pc = check_params(params)) return pc;
   *out = nullptr;
   for (int i = 0; i < n_images; ++i)
     if (!valid_image(imgs[i], params->range_size0)) return FIC_EINVAL;
@@ -893,7 +900,8 @@ int fic_encode(fic_ctx* ctx, const fic_image* imgs, int n_images, const fic_para
 
 int fic_encode_again(fic_ctx* ctx, const fic_image* imgs, int n_images, const fic_params* params,
                      void* stream, fic_code* code) {
-  if (!ctx || !imgs || !code || code->ctx != ctx || check_params(params)) return FIC_EINVAL;
+  if (!ctx || !imgs || !code || code->ctx != ctx || !params) return FIC_EINVAL;
+  if (const int pc = check_params(params)) return pc;
   if (!code_compatible(code, imgs, n_images, params)) return FIC_EINVAL;
   for (int i = 0; i < n_images; ++i)
     if (!valid_image(imgs[i], params->range_size0)) return FIC_EINVAL;
@@ -1030,6 +1038,7 @@ int fic_code_quantize_o(fic_code* code, int o_bits) {
 
 int fic_code_bits(const fic_code* code, int image_idx, int o_bits, int64_t* bits) {
   if (!code || !bits || o_bits < 1 || o_bits > 16) return FIC_EINVAL;
+  if (code->prm.s_mode == FIC_S_EXACT) return FIC_EINVAL;  // s from no finite set
   fic_level_stats st[4];
   int rc = fic_code_stats(code, image_idx, st, 4);
   if (rc) return rc;

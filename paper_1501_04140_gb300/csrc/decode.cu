@@ -84,7 +84,7 @@ __global__ void k_decode_step(const fic_transform* __restrict__ codes,
     int si, sj;
     iso_src(t.size, t.iso, i, j, &si, &sj);
     const double* d = cur + (int64_t)(t.dom_y + 2 * si) * W + (t.dom_x + 2 * sj);
-    const double s = __ddiv_rn((double)t.p, (double)t.q);
+    const double s = t.s;  // p / q, or Eq. 2's s of the exact-s mode
     double m = __dadd_rn(__dadd_rn(__dadd_rn(d[0], d[1]), d[W]), d[W + 1]);
     m = __dmul_rn(m, 0.25);
     double v = __dadd_rn(__dmul_rn(s, m), t.o);

@@ -73,7 +73,7 @@ __global__ void k_check_codes(const fic_transform* __restrict__ codes, int64_t n
     const bool size_ok = b == 2 || b == 4 || b == 8 || b == 16;
     const bool ok = size_ok && t.x >= 0 && t.y >= 0 && t.x <= W - b && t.y <= H - b &&
                     t.dom_x >= 0 && t.dom_y >= 0 && t.dom_x <= W - 2 * b &&
-                    t.dom_y <= H - 2 * b && t.iso >= 0 && t.iso < 8 && t.q > 0;
+                    t.dom_y <= H - 2 * b && t.iso >= 0 && t.iso < 8 && t.s >= 0.0 && t.s <= 1.0;
     if (!ok) atomicAdd(bad, 1);
   }
 }

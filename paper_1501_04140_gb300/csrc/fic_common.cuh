@@ -74,14 +74,40 @@ struct SSet {
   int m;            // |S|
   int q;            // common denominator
   int grid;         // 1: grid k/(M-1) (convex shortcut), 0: explicit list
+  int exact;        // 1: Eq. 2's s of every pair, clamped to [0, 1] (m = 1)
   int p[kMaxS];     // numerators
 };
 
-// Exact lexicographic candidate: score first, then the tie-break key.
+// Exact lexicographic candidate: score first, then the tie-break key.  In
+// the exact-s mode the score is the pair's C = n <r, Ds> - sum r sum Ds and
+// the order is exact_better's (the domain's V comes with it).
 struct Cand {
-  int64_t score;    // E' (exact, tensor path) or float bits (fp32 path)
+  int64_t score;    // E' (exact, tensor path), C (exact s) or float bits (fp32 path)
   int64_t key;      // (pos * 8 + iso) * |S| + s_idx
 };
+
+// Exact-s mode: with the pair's C and the domain's V = n sum Ds^2 - (sum Ds)^2
+// the clamped Eq. 2 gives n E = A - G, G = 0 (C <= 0: s = 0), C^2 / V
+// (0 < 4C < V: s = 4C / V) or (8C - V) / 16 (4C >= V: s = 1); A is the
+// range's, so a larger G is a smaller E.  G as a fraction num / den.
+struct GFrac {
+  __int128 num;
+  int64_t den;
+};
+__host__ __device__ inline GFrac exact_g(int64_t C, int64_t V) {
+  if (C <= 0 || V <= 0) return GFrac{0, 1};
+  if (4 * C >= V) return GFrac{(__int128)(8 * C - V), 16};
+  return GFrac{(__int128)C * C, V};  // C^2 <= 2^68, times a den <= 2^37 below
+}
+// a better than b: larger G, then the lower key; INT64_MAX keys are "none".
+__host__ __device__ inline bool exact_better(int64_t Ca, int64_t Va, int64_t ka, int64_t Cb,
+                                             int64_t Vb, int64_t kb) {
+  if (ka == INT64_MAX) return false;
+  if (kb == INT64_MAX) return true;
+  const GFrac a = exact_g(Ca, Va), b = exact_g(Cb, Vb);
+  const __int128 l = a.num * b.den, r = b.num * a.den;
+  return l > r || (l == r && ka < kb);
+}
 
 // ---------------------------------------------------------------- helpers
 __host__ __device__ inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }

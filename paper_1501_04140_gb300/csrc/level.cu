@@ -165,7 +165,7 @@ k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec
                const int32_t* __restrict__ chunks, const Cand* __restrict__ part, int iso_rows,
                SSet S, int level, const PlanMeta* __restrict__ meta, uint32_t* __restrict__ status,
                fic_transform* __restrict__ res, double e_thr, int last, uint8_t* __restrict__ acc,
-               int32_t* __restrict__ acc_cnt, int32_t* __restrict__ rej_cnt) {
+               int32_t* __restrict__ acc_cnt, int32_t* __restrict__ rej_cnt, PosMoments pm) {
   constexpr int n = B * B;
   const int lane = threadIdx.x & 31;
   const int64_t N = *n_act;
@@ -181,16 +181,28 @@ k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec
     const int rr = (int)(l % kTileRanges);
     const int nc = overflow ? 0 : chunks[im];
     Cand best{INT64_MAX, INT64_MAX};
+    int64_t bv = 0;  // exact s: the best's V
     for (int e = lane; e < nc * iso_rows; e += 32) {
       const int c = e / iso_rows, k = e % iso_rows;
-      cand_min(best, part[((item_off[im] + m * nc + c) * kTileRanges + rr) * iso_rows + k]);
+      const Cand x = part[((item_off[im] + m * nc + c) * kTileRanges + rr) * iso_rows + k];
+      if (S.exact) {
+        const int64_t xv = x.key == INT64_MAX ? 0 : pos_v(pm, im, x.key >> 3, n);
+        if (exact_better(x.score, xv, x.key, best.score, bv, best.key)) best = x, bv = xv;
+      } else {
+        cand_min(best, x);
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       Cand x;
       x.score = __shfl_xor_sync(0xffffffffu, best.score, o);
       x.key = __shfl_xor_sync(0xffffffffu, best.key, o);
-      cand_min(best, x);
+      const int64_t xv = __shfl_xor_sync(0xffffffffu, bv, o);
+      if (S.exact) {
+        if (exact_better(x.score, xv, x.key, best.score, bv, best.key)) best = x, bv = xv;
+      } else {
+        cand_min(best, x);
+      }
     }
     const ImgDev I = imgs[im];
     const bool bad = best.key == INT64_MAX || best.key < 0 ||
@@ -228,24 +240,47 @@ k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec
         sdd2 += __shfl_xor_sync(0xffffffffu, sdd2, o);
         cor += __shfl_xor_sync(0xffffffffu, cor, o);
       }
-      const int64_t p = S.p[s_idx], q = S.q;
       const int64_t A = n * sr2 - sr * sr;
       const int64_t C = n * cor - sr * sdd;
       const int64_t V = n * sdd2 - sdd * sdd;
-      // 16 q^2 n^2 E = n (16 q^2 A - 8 p q C + p^2 V)
-      const int64_t enum_ = (int64_t)n * (16 * q * q * A - 8 * p * q * C + p * p * V);
       t.dom_index = pos;
       t.dom_x = dx;
       t.dom_y = dy;
       t.iso = iso;
-      t.s_idx = s_idx;
-      t.p = (int32_t)p;
-      t.q = (int32_t)q;
-      t.e_num = enum_;
-      t.o_num = 4 * q * sr - p * sdd;  // Eq. 3 times 4 q n
-      t.e = (double)enum_ / (16.0 * (double)(q * q) * (double)n * (double)n);
-      t.s = (double)p / (double)q;
-      t.o = (double)t.o_num / (4.0 * (double)q * (double)n);
+      if (S.exact) {
+        // Eq. 2's s clamped to [0, 1] as sn / sd; Eq. 3's o; E in the
+        // moment form n E = A - G (double operations in this order)
+        int64_t sn = 0, sd = 1;
+        if (C > 0 && V > 0) {
+          if (4 * C >= V) sn = 1;
+          else sn = 4 * C, sd = V;
+        }
+        t.s_idx = 0;
+        t.p = t.q = 0;
+        t.e_num = 0;
+        t.o_num = 0;
+        t.s = __ddiv_rn((double)sn, (double)sd);
+        t.o = __ddiv_rn((double)(4 * sd * sr - sn * sdd), __dmul_rn(__dmul_rn(4.0, (double)sd), (double)n));
+        if (sn == 0)
+          t.e = __ddiv_rn((double)A, (double)n);
+        else if (sn == sd)
+          t.e = __ddiv_rn((double)(16 * A - 8 * C + V), __dmul_rn(16.0, (double)n));
+        else
+          t.e = __ddiv_rn(__dsub_rn((double)A, __ddiv_rn(__dmul_rn((double)C, (double)C), (double)V)),
+                          (double)n);
+      } else {
+        const int64_t p = S.p[s_idx], q = S.q;
+        // 16 q^2 n^2 E = n (16 q^2 A - 8 p q C + p^2 V)
+        const int64_t enum_ = (int64_t)n * (16 * q * q * A - 8 * p * q * C + p * p * V);
+        t.s_idx = s_idx;
+        t.p = (int32_t)p;
+        t.q = (int32_t)q;
+        t.e_num = enum_;
+        t.o_num = 4 * q * sr - p * sdd;  // Eq. 3 times 4 q n
+        t.e = (double)enum_ / (16.0 * (double)(q * q) * (double)n * (double)n);
+        t.s = (double)p / (double)q;
+        t.o = (double)t.o_num / (4.0 * (double)q * (double)n);
+      }
     } else {  // no candidate (plan overflow): flagged, never read as a map
       t.dom_index = -1;
       t.e = INFINITY;
@@ -269,7 +304,7 @@ int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const in
                         const int32_t* chunks, const Cand* part, int iso_rows, const SSet& S,
                         int level, const PlanMeta* meta, uint32_t* status, fic_transform* res,
                         double rms, int last, uint8_t* acc, int32_t* acc_cnt, int32_t* rej_cnt,
-                        cudaStream_t st) {
+                        const PosMoments& pm, cudaStream_t st) {
   const int threads = 32 * kReduceWarps;
   int grid = (int)ceil_div64(cap > 0 ? cap : 1, kReduceWarps);
   if (grid > 65535) grid = 65535;
@@ -278,7 +313,7 @@ int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const in
   k_reduce_final<BB><<<grid, threads, 0, st>>>(imgs, rec, n_act, act_off, pool_off, n_images,  \
                                                L, sel, item_off, chunks, part, iso_rows, S,   \
                                                level, meta, status, res, e_thr, last, acc,    \
-                                               acc_cnt, rej_cnt)
+                                               acc_cnt, rej_cnt, pm)
   switch (B) {
     case 16: FIC_RF(16); break;
     case 8: FIC_RF(8); break;

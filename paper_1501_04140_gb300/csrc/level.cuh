@@ -12,6 +12,20 @@ struct PlanMeta {
 };
 
 // Everything a matcher launch needs (device pointers).
+// Per pool position (kept or not): sum Ds and sum Ds^2 of the domain's 2x2
+// sums, for the V = n sum Ds^2 - (sum Ds)^2 that the exact-s order needs of a
+// candidate known only by its key (pos * 8 + iso).
+struct PosMoments {
+  const int32_t* sd;
+  const int32_t* sq;
+  const int64_t* off;  // n_images + 1 (positions)
+};
+__device__ inline int64_t pos_v(const PosMoments& pm, int im, int64_t pos, int n) {
+  const int64_t g = pm.off[im] + pos;
+  const int64_t s = pm.sd[g], s2 = pm.sq[g];
+  return (int64_t)n * s2 - s * s;
+}
+
 struct MatchArgs {
   int B, n, Kp, n_images;
   SSet S;
@@ -37,6 +51,7 @@ struct MatchArgs {
   Cand* part;                       // per item: 16 ranges x 8 isometry rows (FP32 path)
                                     // or 16 ranges (tensor path)
   uint32_t* status;                 // device status word
+  PosMoments pm;                    // the exact-s mode's V of a key
 };
 
 int launch_range_pack(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
@@ -65,7 +80,7 @@ int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const in
                         const int32_t* chunks, const Cand* part, int iso_rows, const SSet& S,
                         int level, const PlanMeta* meta, uint32_t* status, fic_transform* res,
                         double rms, int last, uint8_t* acc, int32_t* acc_cnt, int32_t* rej_cnt,
-                        cudaStream_t st);
+                        const PosMoments& pm, cudaStream_t st);
 
 int launch_split(const fic_transform* res, const RangeRec* rec, const int64_t* n_act, int64_t cap,
                  int B, int n_images, uint8_t* acc, int32_t* acc_cnt,

@@ -151,7 +151,7 @@ struct TcCfg {
   static_assert(BYTES + 128 <= 227 * 1024, "shared memory");
 };
 
-constexpr int MODE_M1 = 0, MODE_M2 = 1, MODE_GRID = 2;
+constexpr int MODE_M1 = 0, MODE_M2 = 1, MODE_GRID = 2, MODE_EXACT = 3;
 
 struct ItemGeo {
   int im, nr, t0, t1, nkept;
@@ -197,6 +197,30 @@ __device__ inline int item_tile(const ItemGeo& g, int k) {
 __device__ inline float thr_of(int64_t e, float inv_up, float inv_dn, float delta) {
   const float ef = __ll2float_ru(e);
   return __fadd_ru(__fmul_ru(ef, ef >= 0.f ? inv_up : inv_dn), delta);
+}
+
+// Exact-s mode.  A pair's y = C / n is the FMA y above, rounded once: |y -
+// C / n| <= 2^-24 |y|.  Below the clamp point (4C < V: y < Yc = V / (4 n))
+// G = y^2 n^2 / V, computed as (y y) F0 with F0 = n^2 / V rounded: relative
+// error < 5 2^-24; at and above it G = n y / 2 - V / 16, as an FMA with
+// b = V / 16 rounded: error < 2^-23 (n |y| / 2 + b + G); picking the wrong
+// branch next to the clamp point costs (4C - V)^2 / (16 V), below 2^-46 V
+// there; y <= 0 gives G = 0 exactly.  So U = g + 2^-18 (g + n |y| / 2 + b)
+// bounds G from above (rounding of U included).  The screen's score is -U:
+// a pair is skipped only when U stays below a lower bound of the exact G of
+// a candidate already kept, i.e. when it can neither beat nor tie it.
+constexpr float kExactErr = 0x1p-18f;
+
+// Threshold of an exact-s candidate (C, V): -(a lower bound of its exact G).
+__device__ inline float thr_exact(int64_t C, int64_t V) {
+  double gd = 0.0;
+  if (C > 0 && V > 0) {
+    if (4 * C >= V)
+      gd = (double)(8 * C - V) / 16.0;                 // exact (< 2^53)
+    else
+      gd = ((double)C * (double)C) / (double)V;      // within 2 ulps
+  }
+  return -__double2float_rd(gd * (1.0 - 0x1p-50));
 }
 
 template <int B, int MODE>
@@ -432,7 +456,9 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           wv = (float)m.srp * (1.0f / n);
           // rounding bound of this range's float scores (score units): 4x
           // the bound derived above; the grid uses the level-wide margin
-          if (MODE == MODE_GRID) {
+          if (MODE == MODE_EXACT) {
+            dv = 0.f;  // per-pair bounds in the score itself
+          } else if (MODE == MODE_GRID) {
             dv = a.delta;
           } else {
             const double pmx = (double)(MODE == MODE_M2 ? max(a.S.p[0], a.S.p[1]) : a.S.p[0]);
@@ -495,6 +521,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
         const float nX = -sX[dl];
         const float F0 = sX[kTileDoms + dl];
         const float F1 = sX[2 * kTileDoms + dl];
+        const float F2 = MODE == MODE_EXACT ? sX[3 * kTileDoms + dl] : 0.f;
         const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * Cf::NKC * kTileRows);
 
         auto load = [&](int ch, uint32_t(&r)[32]) {
@@ -506,10 +533,20 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           }
         };
 
+        // exact-s mode: -(upper bound of G), see kExactErr (F0 = n^2 / V,
+        // F1 = V / (4 n), F2 = V / 16)
+        auto exact_sc = [&](float y) -> float {
+          constexpr float hn = 0.5f * n;
+          const float gy = y > 0.f ? (y >= F1 ? fmaf(hn, y, -F2) : (y * y) * F0) : 0.f;
+          return -fmaf(kExactErr, gy + fmaf(hn, fabsf(y), F2), gy);
+        };
+
         // float score of a pair from its largest correlation and the range's w
         auto score = [&](float cmax, float wr) -> float {
           const float y = fmaf(nX, wr, cmax);
-          if constexpr (MODE == MODE_GRID) {
+          if constexpr (MODE == MODE_EXACT) {
+            return exact_sc(y);
+          } else if constexpr (MODE == MODE_GRID) {
             float p = rintf(y * F1);
             p = fminf(fmaxf(p, 0.f), qf);
             return p * fmaf(p, F0, -y);
@@ -527,7 +564,9 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           cmax = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
                        ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
           const float y = fmaf(nX, wr, cmax);
-          if constexpr (MODE == MODE_GRID) {
+          if constexpr (MODE == MODE_EXACT) {
+            sc = exact_sc(y);
+          } else if constexpr (MODE == MODE_GRID) {
             float p = rintf(y * F1);
             p = fminf(fmaxf(p, 0.f), qf);
             sc = p * fmaf(p, F0, -y);
@@ -542,13 +581,23 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
         // exact score of this lane's pair: the isometry with the largest
         // correlation (k = 0 where p = 0), every s that can win
         auto pair_exact = [&](const float* v, float cmax, float wr, const DomRec& dr,
-                              int64_t& be, int64_t& bk) {
+                              int64_t& be, int64_t& bv, int64_t& bk) {
           int kmax = 7;
 #pragma unroll
           for (int k = 6; k >= 0; --k)
             if (v[k] == cmax) kmax = k;
           const int64_t srp_r = (int64_t)(int)(wr * (float)n);
           const int64_t C = ((int64_t)(int)cmax << LOGN) - srp_r * (int64_t)dr.sdp;
+          if constexpr (MODE == MODE_EXACT) {
+            // the isometry of the largest correlation (k = 0 when G = 0)
+            const int64_t key = (int64_t)dr.pos * 8 + (C > 0 && dr.v > 0 ? kmax : 0);
+            if (exact_better(C, dr.v, key, be, bv, bk)) {
+              be = C;
+              bv = dr.v;
+              bk = key;
+            }
+            return;
+          }
           auto cand = [&](int64_t p, int si) {
             const int64_t e = p * p * dr.v - 8 * p * qv * C;
             const int64_t key = ((int64_t)dr.pos * 8 + (p > 0 ? kmax : 0)) * m_s + si;
@@ -567,12 +616,48 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           }
         };
 
+        // the warp's best candidate (every lane ends with it): from the one
+        // lane that scored, or a butterfly over all of them
+        auto warp_best = [&](int64_t& be, int64_t& bv, int64_t& bk, unsigned bal) {
+          if (__popc(bal) == 1) {
+            const int src = __ffs(bal) - 1;
+            be = __shfl_sync(0xffffffffu, be, src);
+            bk = __shfl_sync(0xffffffffu, bk, src);
+            if constexpr (MODE == MODE_EXACT) bv = __shfl_sync(0xffffffffu, bv, src);
+          } else {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              const int64_t e2 = __shfl_xor_sync(0xffffffffu, be, o);
+              const int64_t k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+              if constexpr (MODE == MODE_EXACT) {
+                const int64_t v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+                if (exact_better(e2, v2, k2, be, bv, bk)) {
+                  be = e2;
+                  bv = v2;
+                  bk = k2;
+                }
+              } else if (e2 < be || (e2 == be && k2 < bk)) {
+                be = e2;
+                bk = k2;
+              }
+            }
+          }
+        };
+
         // this warp's best of range r and the shared thresholds, from the
         // warp's best candidate (held by every lane)
-        auto resolve = [&](int r, int64_t be, int64_t bk) {
+        auto resolve = [&](int r, int64_t be, int64_t bv, int64_t bk) {
           const Cand cur = mybest[r];
-          if (be < cur.score || (be == cur.score && bk < cur.key)) {
-            const float to = thr_of(be, inv_up, inv_dn, sDelta[r]);
+          bool better;
+          if constexpr (MODE == MODE_EXACT) {
+            const int64_t vc = cur.key == INT64_MAX ? 0 : pos_v(a.pm, g.im, cur.key >> 3, n);
+            better = exact_better(be, bv, bk, cur.score, vc, cur.key);
+          } else {
+            better = be < cur.score || (be == cur.score && bk < cur.key);
+          }
+          if (better) {
+            const float to = MODE == MODE_EXACT ? thr_exact(be, bv)
+                                                : thr_of(be, inv_up, inv_dn, sDelta[r]);
             __syncwarp();
             if (lane == 0) {
               mybest[r] = Cand{be, bk};
@@ -606,30 +691,19 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
             const bool mine = (fl >> j) & 1u;
             if (!__any_sync(0xffffffffu, mine)) continue;
             const int r = ch * RPC + j;
-            float mn = mine ? sl[j] : INFINITY;
+            bool need = mine;  // exact s: every flagged lane (no shared margin)
+            if constexpr (MODE != MODE_EXACT) {
+              float mn = mine ? sl[j] : INFINITY;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            const float lim = __fadd_ru(mn, 2.0f * sDelta[r]);
-            const bool need = mine && sl[j] <= lim;
-            const unsigned bal = __ballot_sync(0xffffffffu, need);
-            int64_t be = INT64_MAX, bk = INT64_MAX;
-            if (need) pair_exact(cl + 8 * j, cml[j], wl[j], sDom[dl], be, bk);
-            if (__popc(bal) == 1) {
-              const int src = __ffs(bal) - 1;
-              be = __shfl_sync(0xffffffffu, be, src);
-              bk = __shfl_sync(0xffffffffu, bk, src);
-            } else {
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) {
-                const int64_t e2 = __shfl_xor_sync(0xffffffffu, be, o);
-                const int64_t k2 = __shfl_xor_sync(0xffffffffu, bk, o);
-                if (e2 < be || (e2 == be && k2 < bk)) {
-                  be = e2;
-                  bk = k2;
-                }
-              }
+              for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+              const float lim = __fadd_ru(mn, 2.0f * sDelta[r]);
+              need = mine && sl[j] <= lim;
             }
-            resolve(r, be, bk);
+            const unsigned bal = __ballot_sync(0xffffffffu, need);
+            int64_t be = INT64_MAX, bv = 0, bk = INT64_MAX;
+            if (need) pair_exact(cl + 8 * j, cml[j], wl[j], sDom[dl], be, bv, bk);
+            warp_best(be, bv, bk, bal);
+            resolve(r, be, bv, bk);
           }
         };
         auto chunk = [&](int ch, const uint32_t* rg) {
@@ -696,7 +770,7 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
                 cm[j] = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
                               ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
               }
-              if constexpr (MODE == MODE_GRID) {
+              if constexpr (MODE == MODE_GRID || MODE == MODE_EXACT) {
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
                   const float sa = score(cm[j], wv[j]), sb = score(cm[j + 1], wv[j + 1]);
@@ -733,30 +807,19 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
               const float scj = score(cmj, sW[r]);
               const bool mine = dvalid && scj <= sThr[r];
               if (!__any_sync(0xffffffffu, mine)) continue;
-              float mn = mine ? scj : INFINITY;
+              bool need = mine;  // exact s: every flagged lane (no shared margin)
+              if constexpr (MODE != MODE_EXACT) {
+                float mn = mine ? scj : INFINITY;
 #pragma unroll
-              for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-              const float lim = __fadd_ru(mn, 2.0f * sDelta[r]);
-              const bool need = mine && scj <= lim;
-              const unsigned bal = __ballot_sync(0xffffffffu, need);
-              int64_t be = INT64_MAX, bk = INT64_MAX;
-              if (need) pair_exact(v, cmj, sW[r], dr, be, bk);
-              if (__popc(bal) == 1) {
-                const int src = __ffs(bal) - 1;
-                be = __shfl_sync(0xffffffffu, be, src);
-                bk = __shfl_sync(0xffffffffu, bk, src);
-              } else {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                  const int64_t e2 = __shfl_xor_sync(0xffffffffu, be, o);
-                  const int64_t k2 = __shfl_xor_sync(0xffffffffu, bk, o);
-                  if (e2 < be || (e2 == be && k2 < bk)) {
-                    be = e2;
-                    bk = k2;
-                  }
-                }
+                for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                const float lim = __fadd_ru(mn, 2.0f * sDelta[r]);
+                need = mine && scj <= lim;
               }
-              resolve(r, be, bk);
+              const unsigned bal = __ballot_sync(0xffffffffu, need);
+              int64_t be = INT64_MAX, bv = 0, bk = INT64_MAX;
+              if (need) pair_exact(v, cmj, sW[r], dr, be, bv, bk);
+              warp_best(be, bv, bk, bal);
+              resolve(r, be, bv, bk);
             }
           }
           ptx::tc_fence_before();
@@ -793,9 +856,15 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
       ptx::named_bar_sync(1, epi_threads);
       if (ew == 0 && lane < kTileRanges) {
         Cand best{INT64_MAX, INT64_MAX};
+        int64_t bv = 0;
         for (int o = 0; o < Cf::Wp::EPI_WARPS; ++o) {
           const Cand x = wbest[o * kTileRanges + lane];
-          if (x.score < best.score || (x.score == best.score && x.key < best.key)) best = x;
+          if constexpr (MODE == MODE_EXACT) {
+            const int64_t xv = x.key == INT64_MAX ? 0 : pos_v(a.pm, g.im, x.key >> 3, n);
+            if (exact_better(x.score, xv, x.key, best.score, bv, best.key)) best = x, bv = xv;
+          } else if (x.score < best.score || (x.score == best.score && x.key < best.key)) {
+            best = x;
+          }
         }
         if (lane >= g.nr) best = Cand{INT64_MAX, INT64_MAX};
         a.part[g.pidx * kTileRanges + lane] = best;
@@ -831,7 +900,8 @@ static int prepare_BM() {
 
 template <int B>
 static int prepare_B() {
-  return prepare_BM<B, MODE_M1>() | prepare_BM<B, MODE_M2>() | prepare_BM<B, MODE_GRID>();
+  return prepare_BM<B, MODE_M1>() | prepare_BM<B, MODE_M2>() | prepare_BM<B, MODE_GRID>() |
+         prepare_BM<B, MODE_EXACT>();
 }
 
 // Opt the matcher kernels in to their shared memory (once per device, before
@@ -842,6 +912,7 @@ int match_tc_prepare() {
 
 template <int B>
 static int launch_tc_B(const MatchArgs& a, int grid, cudaStream_t st) {
+  if (a.S.exact) return launch_tc_BM<B, MODE_EXACT>(a, grid, st);
   if (a.S.grid) return launch_tc_BM<B, MODE_GRID>(a, grid, st);
   if (a.S.m > 1) return launch_tc_BM<B, MODE_M2>(a, grid, st);
   return launch_tc_BM<B, MODE_M1>(a, grid, st);

@@ -23,6 +23,12 @@ namespace fic {
 // ---------------------------------------------------------------- S sets
 void make_sset(int s_mode, int grid_samples, int B, SSet* o) {
   *o = SSet{};
+  if (s_mode == FIC_S_EXACT) {  // one "s" per pair, found from its moments
+    o->exact = 1;
+    o->m = 1;
+    o->q = 1;
+    return;
+  }
   if (s_mode == FIC_S_GRID) {
     o->grid = 1;
     o->m = grid_samples;
@@ -961,8 +967,14 @@ k_pack_domains(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
       // largest u of the level (non-negative floats order as their bits):
       // bounds the scores' rounding errors in the matcher
       atomicMax(&s_umax, __float_as_uint(__double2float_ru(u)));
-      float f0, f1;
-      if (S.grid) {
+      float f0, f1, f2 = 0.0f;
+      if (S.exact) {
+        // exact s: G of the pair is y^2 n^2 / V below the clamp point
+        // y = V / (4 n) and n y / 2 - V / 16 above it (y = C / n)
+        f0 = r.v > 0 ? (float)((double)n * n / (double)r.v) : 0.0f;
+        f1 = (float)((double)r.v / (4.0 * n));
+        f2 = (float)((double)r.v / 16.0);
+      } else if (S.grid) {
         f0 = (float)u;
         f1 = r.v > 0 ? (float)(4.0 * S.q * n / (double)r.v) : 0.0f;
       } else {
@@ -973,13 +985,13 @@ k_pack_domains(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
       ft[0] = (float)r.sdp;
       ft[kTileDoms] = f0;
       ft[2 * kTileDoms] = f1;
-      ft[3 * kTileDoms] = 0.0f;
+      ft[3 * kTileDoms] = f2;
       if (B <= 8 && tile_blk) {  // the same records inside the tile block
         float* fb = (float*)(tile_blk + tc_op_bytes(B)) + (slot & 127);
         fb[0] = (float)r.sdp;
         fb[kTileDoms] = f0;
         fb[2 * kTileDoms] = f1;
-        fb[3 * kTileDoms] = 0.0f;
+        fb[3 * kTileDoms] = f2;
         ((DomRec*)(tile_blk + tc_op_bytes(B) + 4 * kTileDoms * 4))[slot & 127] = r;
       }
     }

@@ -28,6 +28,7 @@ FIC_ERANGE = -6
 
 FIC_S_PREDEFINED = 0
 FIC_S_GRID = 1
+FIC_S_EXACT = 2
 FIC_PREC_TENSOR = 0
 FIC_PREC_FP32 = 1
 

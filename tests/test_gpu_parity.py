@@ -180,6 +180,10 @@ ENC_CASES = [
     (64, 64, 25, 1, dict(range_size0=4, n_levels=2, domain_step=2, rms_threshold=3.0)),
     (96, 96, 26, 1, dict(pool_size=64)),
     (64, 64, 27, 1, dict(pool_size=32, s_mode=1, grid_samples=10)),
+    # exact s (Eq. 2 per pair, clamped to [0, 1])
+    (96, 96, 28, 1, dict(s_mode=2)),
+    (64, 64, 29, 1, dict(s_mode=2, range_size0=8, n_levels=3, domain_step=1)),
+    (64, 96, 30, 0, dict(s_mode=2, rms_threshold=4.0, entropy_percentile=0.25)),
 ]
 
 
@@ -214,6 +218,31 @@ def test_encode_parity_tensor(case):
     np.testing.assert_array_equal(dec, oracle.to_u8(ref_f))
     assert code.iters == it
     code.free()
+
+
+def test_encode_exact_s_ramp_and_errors():
+    """Exact s on the GPU: the ramp f(x, y) = x is exact at the first level
+    (s = 1/2, E = 0, as the oracle); FP32 precision is refused and the stored
+    form's bit count is undefined for it."""
+    fic = _fic()
+    ctx = G.ctx()
+    img = np.tile(np.arange(64, dtype=np.uint8), (64, 1))
+    p = _enc_params(fic, "tensor", dict(s_mode=2, rms_threshold=0.0))
+    code = ctx.encode(G.dev(img), p)
+    got = code.transforms(0)
+    ref, _ = oracle.encode(img, G.oracle_params(p))
+    assert len(got) == len(ref) == 16
+    assert np.all(got["e"] == 0.0) and np.all(got["s"] == 0.5)
+    for f in ("dom_index", "iso", "s", "o", "e"):
+        np.testing.assert_array_equal(got[f], ref[f], err_msg=f)
+    np.testing.assert_array_equal(code.decode(0), img)
+    with pytest.raises(fic.FicError) as e:
+        code.bits(0, 7)
+    assert e.value.status == fic.FIC_EINVAL
+    code.free()
+    with pytest.raises(fic.FicError) as e:
+        ctx.encode(G.dev(img), _enc_params(fic, "fp32", dict(s_mode=2)))
+    assert e.value.status == fic.FIC_EUNSUPPORTED
 
 
 @pytest.mark.parametrize("case", [0, 1, 4])
