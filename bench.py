@@ -262,6 +262,78 @@ def run_tables(args):
     return 0
 
 
+# ------------------------------------------------------------------ s histogram
+def _kmeans_1d(x, k, iters=50):
+    """Lloyd's k-means on the line from the quantile starts (k = 1: the mean)."""
+    import numpy as np
+    c = np.quantile(x, [(i + 0.5) / k for i in range(k)])
+    for _ in range(iters):
+        lab = np.argmin(np.abs(x[:, None] - c[None, :]), axis=1)
+        c = np.array([x[lab == i].mean() if np.any(lab == i) else c[i] for i in range(k)])
+    return np.sort(c)
+
+
+def run_shist(args):
+    """Fig. 3's study on synthetic stand-ins (the paper's test images are not
+    reproduced): a batch of 512x512 images encoded with an exhaustive s
+    search -- Eq. 2's s of every pair (FIC_S_EXACT) and the 10-sample grid of
+    the "existing algorithms" -- and, per quadtree step, the histogram of the
+    s of the saved maps (10 bins over [0, 1]).  Sec. 3.1 reads its predefined
+    sets off such histograms (one value at step 1, two below); the rule here
+    is 1-D k-means of the exact-s values (k = 1 at step 1, 2 below) rounded
+    to 0.1.  Also times each encode (GPU, graph replay) and the PSNR."""
+    import numpy as np
+    import torch
+    from paper_1501_04140_gb300 import build, fic
+    build.build()
+    import oracle
+    from paper_1501_04140_gb300.synth import synth_image
+    ctx = fic.Context(0)
+    stream = torch.cuda.Stream()
+    imgs = [synth_image(512, 512, seed, n_textured=seed % 2) for seed in range(1, 9)]
+    dev = [torch.from_numpy(i).cuda() for i in imgs]
+    out = {"workload": "s histogram (Fig. 3) on 8 synthetic 512x512 images, L = 2, RMS 8",
+           "modes": {}}
+    for name, kw in (("exact s (Eq. 2, clamped)", dict(s_mode=fic.FIC_S_EXACT)),
+                     ("10-sample grid", dict(s_mode=fic.FIC_S_GRID, grid_samples=10)),
+                     ("predefined (Sec. 3.1)", dict(s_mode=fic.FIC_S_PREDEFINED))):
+        p = fic.default_params(**kw)
+        code = ctx.encode(dev, p, stream=stream)
+        times = []
+        for s_ in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.encode_again(code, dev, p, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if s_ >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        per_level = [[] for _ in range(4)]
+        psnr = []
+        for i, img in enumerate(imgs):
+            t = code.transforms(i)
+            for lv in range(4):
+                per_level[lv].extend(t["s"][t["level"] == lv].tolist())
+            psnr.append(oracle.psnr(img, code.decode(i)))
+        levels = []
+        for lv, vals in enumerate(per_level):
+            v = np.asarray(vals)
+            h, _ = np.histogram(v, bins=10, range=(0.0, 1.0))
+            row = {"step": lv + 1, "B": 16 >> lv, "n_maps": int(v.size), "hist_10_bins": h.tolist(),
+                   "median_s": float(np.median(v)) if v.size else None}
+            if kw["s_mode"] == fic.FIC_S_EXACT and v.size:
+                c = _kmeans_1d(v, 1 if lv == 0 else 2)
+                row["derived_set"] = [round(float(min(max(x, 0.1), 0.9)), 1) for x in c]
+            levels.append(row)
+        out["modes"][name] = {"encode_ms_per_batch": statistics.median(times),
+                              "mean_psnr_db": float(np.mean(psnr)), "levels": levels}
+        code.free()
+    print(json.dumps(out))
+    return 0
+
+
 # ------------------------------------------------------------------ decode
 def run_decode(args):
     """Decoder throughput: the 512x512 headline image's saved maps decoded
@@ -512,8 +584,10 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the library's default schedule (by default the library times "
                          "its schedules on the first encode and keeps the fastest)")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["tables", "decode"], default="512",
-                    help="512 (the headline), batch64, 4096, tables or decode (informational runs)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["tables", "decode", "shist"],
+                    default="512",
+                    help="512 (the headline), batch64, 4096, tables, decode or shist "
+                         "(informational runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -523,6 +597,8 @@ def main():
         return run_tables(args)
     if args.workload == "decode":
         return run_decode(args)
+    if args.workload == "shist":
+        return run_shist(args)
     return run_ours(args)
 
 
