@@ -206,7 +206,7 @@ def run_reference(args):
         "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "level-1 ranges"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{per_step} level-1 ranges per step vs {len(kept)} kept "
-                                   f"domains x 8 isometries"},
+                                   f"domains x 8 isometries", "cpu_model": _cpu_model()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -260,6 +260,20 @@ def run_tables(args):
                 code.free()
     print(json.dumps({"workload": "tables", "rows": rows}))
     return 0
+
+
+def _cpu_model():
+    """The host CPU's model name from /proc/cpuinfo (else the machine type)."""
+    import platform
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip().lower() in ("model name", "cpu model", "hardware"):
+                    return v.strip()
+    except OSError:
+        pass
+    return platform.machine()
 
 
 # ------------------------------------------------------------------ s histogram
@@ -489,7 +503,9 @@ def run_ours(args):
                        "bound": "tensor" if tensor_bound else "alu",
                        "achieved": ach, "unit": "TFLOP/s" if tensor_bound else "Top/s",
                        "frac": ach / pk if pk else 0.0,
-                       "matches_per_s": s["matches"] / sec if sec > 0 else 0.0})
+                       "matches_per_s": s["matches"] / sec if sec > 0 else 0.0,
+                       # every (range, domain, isometry, s) of the level's set
+                       "s_evaluations_per_s": n_s * s["matches"] / sec if sec > 0 else 0.0})
     dom = max(range(len(levels)), key=lambda l: levels[l]["matcher_ms"])
     d = levels[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"],
@@ -541,7 +557,8 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "512":
         cores = os.cpu_count() or 1
         v, sample = oracle_rate(img, stats, args.cpu_budget, cores)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "cpu_model": _cpu_model()}
 
     if rank == 0:
         line = {
