@@ -864,8 +864,8 @@ __device__ inline int64_t bpack_index(int64_t slot, int e) {
 // One thread per (kept domain, 8-element K group): the group's 8 downsampled
 // values Ds - 512 (each the sum of a 2x2 pixel block, read as two pixel
 // pairs) go out as one 16-byte store of f16 (at B = 16 the warp of a domain
-// reads row by row instead, see below); the group-0 thread also writes the
-// domain's records.
+// reads row by row instead, see below).  Then one thread per domain writes
+// its records.
 constexpr int kPackThreads = 256;
 
 template <int B>
@@ -949,7 +949,15 @@ k_pack_domains(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off,
       for (int u = 0; u < 8; ++u)
         if (8 * g + u < n) b32[slot * n + 8 * g + u] = (float)v[u];
     }
-    if (g == 0) {
+  }
+  // the domains' records: one thread per slot
+  for (int64_t slot = (int64_t)blockIdx.x * kPackThreads + threadIdx.x; slot < S_tot;
+       slot += (int64_t)gridDim.x * kPackThreads) {
+    const int im = find_segment(slot_off, n_images, slot);
+    if (slot - slot_off[im] >= st[im].nkept) continue;
+    const int32_t pos = kept[slot];
+    uint8_t* tile_blk = bpack ? (uint8_t*)bpack + (slot >> 7) * (int64_t)tc_tile_bytes(B) : nullptr;
+    {
       const int64_t gpos = off[im] + pos;
       const int64_t s = sd[gpos], s2 = sq[gpos];
       DomRec r;
