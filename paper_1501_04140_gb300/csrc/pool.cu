@@ -1,10 +1,14 @@
 // pool.cu -- the entropy-filtered domain pool of one quadtree level (Sec. 2
 // domain pool, Sec. 3 entropy filter) for a batch of images.
 //
-//   k_pool_stats    every 2B x 2B square at step L: its entropy key (Eq. 4-5,
-//                   fixed point), the sum of its 2x2 sums Ds and of Ds^2.
-//   k_sel_*         exact percentile threshold of the keys (radix select,
-//                   5 passes of 9 bits), per image.
+//   k_pool_stats_lane, k_pool_stats_warp16
+//                   every 2B x 2B square at step L: its entropy key (Eq. 4-5,
+//                   fixed point), the sum of its 2x2 sums Ds and of Ds^2,
+//                   sliding along runs of positions.
+//   k_select_compact  per image in one block: the exact percentile (or top-K)
+//                   threshold of the keys and the kept list; pools above 2^20
+//                   positions use k_sel_* (radix select, 5 passes of 9 bits)
+//                   and the multi-block compaction.
 //   compaction      kept = entropy greater than the threshold (key below it),
 //                   ascending raster order; "greater or equal" when that keeps
 //                   nothing.
@@ -67,74 +71,7 @@ int host_key_table(int64_t* dT, int nmax) {
 }
 
 // ---------------------------------------------------------------- pool statistics
-// G lanes per domain (G = min(32, B^2)); each lane takes whole 2x2 cells.
-template <int B>
-struct PoolGeom {
-  static constexpr int n = B * B;
-  static constexpr int G = n < 32 ? n : 32;
-  static constexpr int GPB = 16;             // groups (domains) per block
-  static constexpr int threads = G * GPB;
-};
-
-template <int B>
-__global__ void __launch_bounds__(PoolGeom<B>::threads)
-k_pool_stats(const ImgDev* __restrict__ imgs, const int64_t* __restrict__ off, int n_images,
-             int L, const int64_t* __restrict__ dT_g, int64_t* __restrict__ keys,
-             int32_t* __restrict__ sd, int32_t* __restrict__ sq) {
-  using Gm = PoolGeom<B>;
-  constexpr int G = Gm::G;
-  constexpr int N4 = 4 * B * B;
-  __shared__ uint32_t hist[Gm::GPB][256];
-  __shared__ int64_t dT[N4 + 1];
-  for (int i = threadIdx.x; i <= N4; i += blockDim.x) dT[i] = dT_g[i];
-  for (int i = threadIdx.x; i < Gm::GPB * 256; i += blockDim.x) (&hist[0][0])[i] = 0;
-  __syncthreads();
-
-  const int grp = threadIdx.x / G, gl = threadIdx.x % G;
-  uint32_t* h = hist[grp];
-  const int64_t P_tot = off[n_images];
-  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-  for (int64_t g = (int64_t)blockIdx.x * Gm::GPB + grp; g < P_tot; g += (int64_t)gridDim.x * Gm::GPB) {
-    const int im = find_segment(off, n_images, g);
-    const ImgDev I = imgs[im];
-    const int64_t pos = g - off[im];
-    const int x0 = (int)(pos % I.px) * L, y0 = (int)(pos / I.px) * L;
-    int64_t key = 0;
-    int s = 0, s2 = 0;
-    for (int c = gl; c < B * B; c += G) {
-      const int ci = c / B, cj = c % B;
-      const uint8_t* p = I.pix + (int64_t)(y0 + 2 * ci) * I.pitch + (x0 + 2 * cj);
-      const int v0 = p[0], v1 = p[1], v2 = p[I.pitch], v3 = p[I.pitch + 1];
-      key += dT[atomicAdd(&h[v0], 1u) + 1];
-      key += dT[atomicAdd(&h[v1], 1u) + 1];
-      key += dT[atomicAdd(&h[v2], 1u) + 1];
-      key += dT[atomicAdd(&h[v3], 1u) + 1];
-      const int ds = v0 + v1 + v2 + v3;
-      s += ds;
-      s2 += ds * ds;
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      key += __shfl_xor_sync(gmask, key, o, G);
-      s += __shfl_xor_sync(gmask, s, o, G);
-      s2 += __shfl_xor_sync(gmask, s2, o, G);
-    }
-    __syncwarp(gmask);
-    for (int c = gl; c < B * B; c += G) {  // clear the bins this lane touched
-      const int ci = c / B, cj = c % B;
-      const uint8_t* p = I.pix + (int64_t)(y0 + 2 * ci) * I.pitch + (x0 + 2 * cj);
-      h[p[0]] = 0; h[p[1]] = 0; h[p[I.pitch]] = 0; h[p[I.pitch + 1]] = 0;
-    }
-    __syncwarp(gmask);
-    if (gl == 0) {
-      keys[g] = key;
-      sd[g] = s;
-      sq[g] = s2;
-    }
-  }
-}
-
-// Sliding version: one lane per run of positions along a row (see
+// One lane per run of positions along a row (see
 // pool_run_len), with a lane-private histogram in shared memory (16-bit
 // counts, [grey level][lane], so the lanes of a warp never contend).  The
 // first window of a run is built in full; each next position removes the
