@@ -130,7 +130,7 @@ def _sm_max_mhz():
 # launch per level B on this workload, from one ncu capture of the current
 # kernel (cold caches: the operands' first touch); empty when the kernel has
 # changed since the last capture.
-TRAFFIC = {16: 20126720, 8: 6291200, 4: 3356416, 2: 3049216}
+TRAFFIC = {16: 20128000, 8: 6290944, 4: 3355648, 2: 3051776}
 
 
 def _dist():
@@ -265,15 +265,18 @@ def run_tables(args):
 def _cpu_model():
     """The host CPU's model name from /proc/cpuinfo (else the machine type)."""
     import platform
+    part = None
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 k, _, v = line.partition(":")
                 if k.strip().lower() in ("model name", "cpu model", "hardware"):
                     return v.strip()
+                if k.strip().lower() == "cpu part" and part is None:
+                    part = v.strip()
     except OSError:
         pass
-    return platform.machine()
+    return platform.machine() + (f" (CPU part {part})" if part else "")
 
 
 # ------------------------------------------------------------------ s histogram
