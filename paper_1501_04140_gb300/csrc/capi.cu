@@ -326,13 +326,17 @@ int level_alloc(fic_ctx* ctx, LevelWs& w, const std::vector<fic_image>& ims, int
 // Matching of the active ranges of one level against the level's pool,
 // then the exact map of every range (res).
 // With split >= 0 the reducer also takes the level's split decision (split =
-// 1 on the last level, which accepts every range).
+// 1 on the last level, which accepts every range).  A pool built on another
+// stream joins through pool_ready, after the range operand and before the
+// plan, the first step that reads the pool.
 int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cudaStream_t st,
-                cudaEvent_t* ev = nullptr, int split = -1) {
+                cudaEvent_t* ev = nullptr, int split = -1, cudaEvent_t pool_ready = nullptr) {
   PoolLevel& pl = w.pool;
   const int ni = pl.n_images;
   const bool tc = prm.precision == FIC_PREC_TENSOR;
   const int grid = ctx->nsm;
+  int32_t* tile_acc = split >= 0 ? w.scan_scr.as<int32_t>() : nullptr;
+  const int n_tiles = (int)ceil_div64(w.cap > 0 ? w.cap : 1, kScanTile);
   // range operand (also resets the ranges' shared thresholds) and the plan
   auto pack_plan = [&](int items_per_cta) -> int {
     int rc = launch_range_pack(w.B, pl.img.as<ImgDev>(), w.rec.as<RangeRec>(),
@@ -340,11 +344,12 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
                                w.gthr.as<uint32_t>(), tc ? w.apack.as<uint16_t>() : nullptr,
                                tc ? nullptr : w.a32.as<float>(), st);
     if (rc) return rc;
-    k_plan<<<1, 32, 0, st>>>(ni, w.act_off.as<int64_t>(), w.act_cnt.as<int64_t>(),
-                             pl.sel.as<SelState>(), items_per_cta * grid, w.item_cap, w.mt_cap,
-                             w.meta.as<PlanMeta>(), w.item_off.as<int64_t>(),
-                             w.chunks.as<int32_t>(), w.acc_cnt.as<int32_t>(),
-                             w.rej_cnt.as<int32_t>());
+    if (pool_ready) FIC_CUDA_TRY(cudaStreamWaitEvent(st, pool_ready, 0));
+    k_plan<<<1, 256, 0, st>>>(ni, w.act_off.as<int64_t>(), w.act_cnt.as<int64_t>(),
+                              pl.sel.as<SelState>(), items_per_cta * grid, w.item_cap, w.mt_cap,
+                              w.meta.as<PlanMeta>(), w.item_off.as<int64_t>(),
+                              w.chunks.as<int32_t>(), w.acc_cnt.as<int32_t>(),
+                              w.rej_cnt.as<int32_t>(), tile_acc, n_tiles);
     return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
   };
   MatchArgs a{};
@@ -423,7 +428,7 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
                              w.meta.as<PlanMeta>(), ctx->status.as<uint32_t>(),
                              w.res.as<fic_transform>(), prm.rms_threshold, split > 0 ? 1 : 0,
                              split >= 0 ? w.acc.as<uint8_t>() : nullptr, w.acc_cnt.as<int32_t>(),
-                             w.rej_cnt.as<int32_t>(), a.pm, st);
+                             w.rej_cnt.as<int32_t>(), tile_acc, a.pm, st);
 }
 
 int64_t ranges_at(const std::vector<fic_image>& ims, int B) {
@@ -459,14 +464,13 @@ int encode_device(fic_code* c, cudaStream_t st) {
   const int ni = c->n_images;
   const int B0 = prm.range_size0;
   int rc = FIC_OK;
-  // fork: the pools of levels 1.. on their side streams
-  if (c->n_levels > 1) {
-    FIC_CUDA_TRY(cudaEventRecord(c->fork_ev, st));
-    for (int l = 1; l < c->n_levels; ++l) {
-      FIC_CUDA_TRY(cudaStreamWaitEvent(c->side[l], c->fork_ev, 0));
-      if ((rc = pool_build(c->lv[l].pool, ctx->dT.as<int64_t>(), c->side[l]))) return rc;
-      FIC_CUDA_TRY(cudaEventRecord(c->pool_ev[l], c->side[l]));
-    }
+  // fork: every level's pool on its own side stream; each level joins its
+  // pool before its plan, so level 0's ranges are set up meanwhile
+  FIC_CUDA_TRY(cudaEventRecord(c->fork_ev, st));
+  for (int l = 0; l < c->n_levels; ++l) {
+    FIC_CUDA_TRY(cudaStreamWaitEvent(c->side[l], c->fork_ev, 0));
+    if ((rc = pool_build(c->lv[l].pool, ctx->dT.as<int64_t>(), c->side[l]))) return rc;
+    FIC_CUDA_TRY(cudaEventRecord(c->pool_ev[l], c->side[l]));
   }
   for (int l = 0; l < c->n_levels; ++l) {
     LevelWs& w = c->lv[l];
@@ -479,13 +483,9 @@ int encode_device(fic_code* c, cudaStream_t st) {
                                           w.rec.as<RangeRec>(), w.n_act.as<int64_t>(),
                                           w.act_off.as<int64_t>(), w.act_cnt.as<int64_t>());
     }
-    if (l == 0) {
-      if ((rc = pool_build(pl, ctx->dT.as<int64_t>(), st))) return rc;
-    } else {
-      FIC_CUDA_TRY(cudaStreamWaitEvent(st, c->pool_ev[l], 0));  // join
-    }
     const bool last = (l == c->n_levels - 1);
-    if ((rc = level_match(ctx, w, prm, l, st, c->profile ? c->ev[l] : nullptr, last ? 1 : 0)))
+    if ((rc = level_match(ctx, w, prm, l, st, c->profile ? c->ev[l] : nullptr, last ? 1 : 0,
+                          c->pool_ev[l])))
       return rc;
     LevelWs* nx = last ? nullptr : &c->lv[l + 1];
     rc = launch_split(w.res.as<fic_transform>(), w.rec.as<RangeRec>(), w.n_act.as<int64_t>(), w.cap,
@@ -855,15 +855,14 @@ static int code_setup(fic_ctx* ctx, const fic_image* imgs, int n_images, const f
     int rc = level_alloc(ctx, w, c->dims, B, ranges_at(c->dims, B), *params);
     if (!rc) rc = pool_alloc(w.pool);
     if (rc) return rc;
-    if (l > 0) {
-      // lowest priority: the level chain's own kernels go first
-      int lo = 0, hi = 0;
-      FIC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-      FIC_CUDA_TRY(cudaStreamCreateWithPriority(&c->side[l], cudaStreamNonBlocking, lo));
-      FIC_CUDA_TRY(cudaEventCreateWithFlags(&c->pool_ev[l], cudaEventDisableTiming));
-    }
+    // level 0's pool is on the critical path: the greatest priority; the
+    // later levels' pools the least, so the level chain's kernels go first
+    int lo = 0, hi = 0;
+    FIC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    FIC_CUDA_TRY(cudaStreamCreateWithPriority(&c->side[l], cudaStreamNonBlocking, l == 0 ? hi : lo));
+    FIC_CUDA_TRY(cudaEventCreateWithFlags(&c->pool_ev[l], cudaEventDisableTiming));
   }
-  if (c->n_levels > 1) FIC_CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+  FIC_CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
   return FIC_OK;
 }
 

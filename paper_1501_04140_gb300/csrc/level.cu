@@ -8,7 +8,8 @@
 //                    and Eq. 3 in exact integers for the chosen map, and the
 //                    split decision: accept when E <= n T^2 (last level:
 //                    always), otherwise four children (16 -> 8 -> 4 -> 2);
-//   k_split_offsets + compaction   the saved codes and the next level's ranges.
+//   k_split_scan + k_scan_scatter  the saved codes and the next level's
+//                    ranges, from the reducer's accepted counts per tile.
 #include <math.h>
 
 #include "fic_internal.h"
@@ -17,7 +18,8 @@
 
 namespace fic {
 
-__global__ void __launch_bounds__(1024) k_scan_blocks(int32_t* cnt, int nb, int64_t* total) {
+// One block: exclusive scan of nb counts in place; *total = their sum.
+__device__ void block_scan_counts(int32_t* cnt, int nb, int64_t* total) {
   __shared__ int sw[32];
   __shared__ int tot;
   int64_t carry = 0;
@@ -30,6 +32,10 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(int32_t* cnt, int nb, int6
     __syncthreads();
   }
   if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_blocks(int32_t* cnt, int nb, int64_t* total) {
+  block_scan_counts(cnt, nb, total);
 }
 
 // ---------------------------------------------------------------- range operand
@@ -111,12 +117,17 @@ int launch_range_pack(int B, const ImgDev* imgs, const RangeRec* rec, const int6
 
 // ---------------------------------------------------------------- plan
 // One thread: images are few (<= kMaxImages) and this runs once per level.
+// The block also zeroes the reducer's accepted counts per compaction tile.
 __global__ void k_plan(int n_images, const int64_t* __restrict__ act_off,
                        const int64_t* __restrict__ act_cnt, const SelState* __restrict__ sel,
                        int target_items, int64_t item_cap, int64_t mt_cap, PlanMeta* meta,
                        int64_t* __restrict__ item_off, int32_t* __restrict__ chunks,
-                       int32_t* __restrict__ acc_cnt, int32_t* __restrict__ rej_cnt) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+                       int32_t* __restrict__ acc_cnt, int32_t* __restrict__ rej_cnt,
+                       int32_t* __restrict__ tile_acc, int n_tiles) {
+  if (blockIdx.x != 0) return;
+  if (tile_acc)
+    for (int i = threadIdx.x; i < n_tiles; i += blockDim.x) tile_acc[i] = 0;
+  if (threadIdx.x != 0) return;
   // the split counters of the level start at zero (k_reduce_final adds)
   for (int i = 0; i < n_images; ++i) acc_cnt[i] = 0, rej_cnt[i] = 0;
   int64_t work = 0;
@@ -165,7 +176,8 @@ k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec
                const int32_t* __restrict__ chunks, const Cand* __restrict__ part, int iso_rows,
                SSet S, int level, const PlanMeta* __restrict__ meta, uint32_t* __restrict__ status,
                fic_transform* __restrict__ res, double e_thr, int last, uint8_t* __restrict__ acc,
-               int32_t* __restrict__ acc_cnt, int32_t* __restrict__ rej_cnt, PosMoments pm) {
+               int32_t* __restrict__ acc_cnt, int32_t* __restrict__ rej_cnt,
+               int32_t* __restrict__ tile_acc, PosMoments pm) {
   constexpr int n = B * B;
   const int lane = threadIdx.x & 31;
   const int64_t N = *n_act;
@@ -293,6 +305,7 @@ k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec
         const bool a = last || (t.e <= e_thr);
         acc[g] = a ? 1 : 0;
         atomicAdd(a ? &acc_cnt[im] : &rej_cnt[im], 1);
+        if (a) atomicAdd(&tile_acc[g / kScanTile], 1);
       }
     }
   }
@@ -304,7 +317,8 @@ int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const in
                         const int32_t* chunks, const Cand* part, int iso_rows, const SSet& S,
                         int level, const PlanMeta* meta, uint32_t* status, fic_transform* res,
                         double rms, int last, uint8_t* acc, int32_t* acc_cnt, int32_t* rej_cnt,
-                        const PosMoments& pm, cudaStream_t st) {
+                        int32_t* tile_acc, const PosMoments& pm, cudaStream_t st) {
+  if (acc && !tile_acc) return FIC_EINVAL;
   const int threads = 32 * kReduceWarps;
   int grid = (int)ceil_div64(cap > 0 ? cap : 1, kReduceWarps);
   if (grid > 65535) grid = 65535;
@@ -313,7 +327,7 @@ int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const in
   k_reduce_final<BB><<<grid, threads, 0, st>>>(imgs, rec, n_act, act_off, pool_off, n_images,  \
                                                L, sel, item_off, chunks, part, iso_rows, S,   \
                                                level, meta, status, res, e_thr, last, acc,    \
-                                               acc_cnt, rej_cnt, pm)
+                                               acc_cnt, rej_cnt, tile_acc, pm)
   switch (B) {
     case 16: FIC_RF(16); break;
     case 8: FIC_RF(8); break;
@@ -331,13 +345,17 @@ int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const in
 // (double) e_num / (16 q^2 n^2) against n (T T); the last level accepts
 // everything.)
 
-// Per-image offsets of the codes saved at this level and of the next level's
-// ranges (4 children per split range); images stay in order.
-__global__ void k_split_offsets(int n_images, const int32_t* __restrict__ acc_cnt,
-                                const int32_t* __restrict__ rej_cnt, int64_t* __restrict__ code_off,
-                                int64_t* __restrict__ next_off, int64_t* __restrict__ next_cnt,
-                                int64_t* __restrict__ next_n) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One block: the per-image offsets of the codes saved at this level and of
+// the next level's ranges (4 children per split range; images stay in
+// order), and the exclusive scan of the accepted counts of the compaction
+// tiles, which gives every tile the rank of its first saved code.
+__global__ void __launch_bounds__(1024)
+k_split_scan(int n_images, const int32_t* __restrict__ acc_cnt,
+             const int32_t* __restrict__ rej_cnt, int64_t* __restrict__ code_off,
+             int64_t* __restrict__ next_off, int64_t* __restrict__ next_cnt,
+             int64_t* __restrict__ next_n, int32_t* tile_acc, int n_tiles, int64_t* total) {
+  block_scan_counts(tile_acc, n_tiles, total);
+  if (threadIdx.x != 0) return;
   int64_t a = 0, c = 0;
   for (int i = 0; i < n_images; ++i) {
     code_off[i] = a;
@@ -378,13 +396,14 @@ struct SplitCompact {
 int launch_split(const fic_transform* res, const RangeRec* rec, const int64_t* n_act, int64_t cap,
                  int B, int n_images, uint8_t* acc, int32_t* acc_cnt,
                  int32_t* rej_cnt, int64_t* code_off, fic_transform* codes, RangeRec* next,
-                 int64_t* next_off, int64_t* next_cnt, int64_t* next_n, int32_t* scan_scratch,
+                 int64_t* next_off, int64_t* next_cnt, int64_t* next_n, int32_t* tile_acc,
                  int64_t* total, cudaStream_t st) {
-  k_split_offsets<<<1, 32, 0, st>>>(n_images, acc_cnt, rej_cnt, code_off, next_off, next_cnt,
-                                     next_n);
+  const int nb = (int)ceil_div64(cap > 0 ? cap : 1, kScanTile);
+  k_split_scan<<<1, 1024, 0, st>>>(n_images, acc_cnt, rej_cnt, code_off, next_off, next_cnt,
+                                   next_n, tile_acc, nb, total);
   SplitCompact sc{n_act, acc, res, rec, codes, next, B / 2};
-  FIC_CUDA_TRY(scan_compact(sc, cap, scan_scratch, total, st));
-  return FIC_OK;
+  k_scan_scatter<SplitCompact><<<nb, kScanThreads, 0, st>>>(sc, tile_acc);
+  return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
 }
 
 }  // namespace fic

@@ -72,7 +72,7 @@ __device__ inline float ord_to_thr(uint32_t u) {
 __global__ void k_plan(int n_images, const int64_t* act_off, const int64_t* act_cnt,
                        const SelState* sel, int target_items, int64_t item_cap, int64_t mt_cap,
                        PlanMeta* meta, int64_t* item_off, int32_t* chunks, int32_t* acc_cnt,
-                       int32_t* rej_cnt);
+                       int32_t* rej_cnt, int32_t* tile_acc, int n_tiles);
 
 int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
                         int64_t cap, const int64_t* act_off, const int64_t* pool_off,
@@ -80,12 +80,15 @@ int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const in
                         const int32_t* chunks, const Cand* part, int iso_rows, const SSet& S,
                         int level, const PlanMeta* meta, uint32_t* status, fic_transform* res,
                         double rms, int last, uint8_t* acc, int32_t* acc_cnt, int32_t* rej_cnt,
-                        const PosMoments& pm, cudaStream_t st);
+                        int32_t* tile_acc, const PosMoments& pm, cudaStream_t st);
 
+// The saved codes and the next level's ranges of a level whose reducer took
+// the split decision (acc, the per-image counts and tile_acc, the accepted
+// ranges of every kScanTile-range tile, counted by k_reduce_final).
 int launch_split(const fic_transform* res, const RangeRec* rec, const int64_t* n_act, int64_t cap,
                  int B, int n_images, uint8_t* acc, int32_t* acc_cnt,
                  int32_t* rej_cnt, int64_t* code_off, fic_transform* codes, RangeRec* next,
-                 int64_t* next_off, int64_t* next_cnt, int64_t* next_n, int32_t* scan_scratch,
+                 int64_t* next_off, int64_t* next_cnt, int64_t* next_n, int32_t* tile_acc,
                  int64_t* total, cudaStream_t st);
 
 // Matchers: fill args.part for every planned item.  `grid` persistent CTAs.
