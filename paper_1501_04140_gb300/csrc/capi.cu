@@ -342,7 +342,7 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
     int rc = launch_range_pack(w.B, pl.img.as<ImgDev>(), w.rec.as<RangeRec>(),
                                w.n_act.as<int64_t>(), w.cap, w.Kp, w.mom.as<RangeMom>(),
                                w.gthr.as<uint32_t>(), tc ? w.apack.as<uint16_t>() : nullptr,
-                               tc ? nullptr : w.a32.as<float>(), st);
+                               tc ? nullptr : w.a32.as<float>(), ctx->nsm, st);
     if (rc) return rc;
     if (pool_ready) FIC_CUDA_TRY(cudaStreamWaitEvent(st, pool_ready, 0));
     k_plan<<<1, 256, 0, st>>>(ni, w.act_off.as<int64_t>(), w.act_cnt.as<int64_t>(),
@@ -428,7 +428,7 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
                              w.meta.as<PlanMeta>(), ctx->status.as<uint32_t>(),
                              w.res.as<fic_transform>(), prm.rms_threshold, split > 0 ? 1 : 0,
                              split >= 0 ? w.acc.as<uint8_t>() : nullptr, w.acc_cnt.as<int32_t>(),
-                             w.rej_cnt.as<int32_t>(), tile_acc, a.pm, st);
+                             w.rej_cnt.as<int32_t>(), tile_acc, a.pm, ctx->nsm, st);
 }
 
 int64_t ranges_at(const std::vector<fic_image>& ims, int B) {

@@ -8,9 +8,11 @@
 //                    and Eq. 3 in exact integers for the chosen map, and the
 //                    split decision: accept when E <= n T^2 (last level:
 //                    always), otherwise four children (16 -> 8 -> 4 -> 2);
-//   k_split_scan + k_scan_scatter  the saved codes and the next level's
+//   k_split_scan + k_split_scatter  the saved codes and the next level's
 //                    ranges, from the reducer's accepted counts per tile.
 #include <math.h>
+
+#include <algorithm>
 
 #include "fic_internal.h"
 #include "level.cuh"
@@ -100,11 +102,12 @@ k_range_pack(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec,
 
 int launch_range_pack(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
                       int64_t cap, int Kp, RangeMom* mom, uint32_t* gthr, uint16_t* apack,
-                      float* a32, cudaStream_t st) {
+                      float* a32, int nsm, cudaStream_t st) {
   const int threads = kRangePackThreads;
   const int64_t rpb = threads / (B * B);
-  int grid = (int)ceil_div64(cap > 0 ? cap : 1, rpb);
-  if (grid > 65535) grid = 65535;
+  // grid-stride over the device count: at most 8 resident blocks per SM
+  const int64_t gmax = nsm > 0 ? 8 * (int64_t)nsm : 65535;
+  const int grid = (int)std::min<int64_t>(ceil_div64(cap > 0 ? cap : 1, rpb), gmax);
   switch (B) {
     case 16: k_range_pack<16><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, gthr, apack, a32); break;
     case 8: k_range_pack<8><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, gthr, apack, a32); break;
@@ -317,11 +320,12 @@ int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const in
                         const int32_t* chunks, const Cand* part, int iso_rows, const SSet& S,
                         int level, const PlanMeta* meta, uint32_t* status, fic_transform* res,
                         double rms, int last, uint8_t* acc, int32_t* acc_cnt, int32_t* rej_cnt,
-                        int32_t* tile_acc, const PosMoments& pm, cudaStream_t st) {
+                        int32_t* tile_acc, const PosMoments& pm, int nsm, cudaStream_t st) {
   if (acc && !tile_acc) return FIC_EINVAL;
   const int threads = 32 * kReduceWarps;
-  int grid = (int)ceil_div64(cap > 0 ? cap : 1, kReduceWarps);
-  if (grid > 65535) grid = 65535;
+  // grid-stride over the device count: at most 8 resident blocks per SM
+  const int64_t gmax = nsm > 0 ? 8 * (int64_t)nsm : 65535;
+  const int grid = (int)std::min<int64_t>(ceil_div64(cap > 0 ? cap : 1, kReduceWarps), gmax);
   const double e_thr = (double)(B * B) * (rms * rms);
 #define FIC_RF(BB)                                                                            \
   k_reduce_final<BB><<<grid, threads, 0, st>>>(imgs, rec, n_act, act_off, pool_off, n_images,  \
@@ -393,6 +397,23 @@ struct SplitCompact {
   }
 };
 
+// One thread per range of a kScanTile-range tile (so that the copies of
+// all the tile's ranges are in flight at once): the tile's accepted ranges
+// take consecutive code ranks from the tile's scanned count, the others four
+// children each, both in index order.
+__global__ void __launch_bounds__(kScanTile)
+k_split_scatter(SplitCompact f, const int32_t* __restrict__ tile_off) {
+  __shared__ int sw[32];
+  const int64_t n = f.size();
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  if (base >= n) return;  // uniform per block
+  const int64_t i = base + threadIdx.x;
+  const bool fl = i < n && f.flag(i);
+  const int before = block_excl_scan(fl ? 1 : 0, sw, nullptr);
+  const int64_t r = (int64_t)tile_off[blockIdx.x] + before;
+  if (i < n) f.emit(i, fl ? r : i - r, fl);
+}
+
 int launch_split(const fic_transform* res, const RangeRec* rec, const int64_t* n_act, int64_t cap,
                  int B, int n_images, uint8_t* acc, int32_t* acc_cnt,
                  int32_t* rej_cnt, int64_t* code_off, fic_transform* codes, RangeRec* next,
@@ -402,7 +423,7 @@ int launch_split(const fic_transform* res, const RangeRec* rec, const int64_t* n
   k_split_scan<<<1, 1024, 0, st>>>(n_images, acc_cnt, rej_cnt, code_off, next_off, next_cnt,
                                    next_n, tile_acc, nb, total);
   SplitCompact sc{n_act, acc, res, rec, codes, next, B / 2};
-  k_scan_scatter<SplitCompact><<<nb, kScanThreads, 0, st>>>(sc, tile_acc);
+  k_split_scatter<<<nb, kScanTile, 0, st>>>(sc, tile_acc);
   return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
 }
 
