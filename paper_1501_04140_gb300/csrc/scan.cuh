@@ -1,6 +1,6 @@
 // scan.cuh -- stable stream compaction over index spaces whose length may be
-// known only on the device (used for the kept-domain lists, the saved codes
-// and the child ranges of the quadtree split).
+// known only on the device (the kept-domain lists of pools above 2^20
+// positions), and the block scan that the other compactions share.
 //
 // Three launches: per-block counts of the predicate, one block scanning the
 // counts, and a scatter that gives every selected element its global rank in
