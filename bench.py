@@ -140,6 +140,31 @@ def _dist():
     return ws, rank, local
 
 
+def _barrier(ws: int) -> None:
+    """All ranks meet here (nothing to do on one rank)."""
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest x over the ranks (x itself on one rank): a job is as slow
+    as its slowest replica."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(ws: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: the units of every replica over the slowest
+    rank's time."""
+    return ws * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------ oracle
 def oracle_rate(img, level_stats, budget_s: float, n_threads: int):
     """The oracle's matches/s on a bounded sample: per level, the exhaustive
@@ -434,6 +459,8 @@ def run_ours(args):
             ctx.encode_again(code, d_img, p, stream=stream)
         torch.cuda.synchronize()
         times, prof = [], []
+        _barrier(ws)
+        torch.cuda.synchronize()
         with Clocks(local) as clk:
             for _ in range(steps):
                 l2_flush.zero_()  # inputs are smaller than L2: flush between steps
@@ -452,6 +479,8 @@ def run_ours(args):
                         print(f"in-graph profile failed ({e}); timing kernels outside it",
                               file=sys.stderr)
                         prof = None
+        torch.cuda.synchronize()
+        _barrier(ws)
         if profile and prof is None:
             prof = []
             for _ in range(max(3, steps // 2)):
@@ -470,14 +499,8 @@ def run_ours(args):
     psnr = oracle.psnr(img, dec)  # the first image
 
     # max over ranks
-    t_max = ms
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = ws * matches / (t_max * 1e-3)
+    t_max = _max_over_ranks(ms, ws, "cuda")
+    value = _job_rate(ws, matches, t_max * 1e-3)
 
     # roofline of the dominant kernel: the tensor matcher at its costliest
     # level.  Per match (range x isometry x kept domain) it does 2n MMA flops
@@ -552,7 +575,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         if s >= e2e_warm:
             e2e.append(t1 - t0)
-    e2e_v = ws * matches / statistics.mean(e2e)
+    e2e_v = _job_rate(ws, matches, _max_over_ranks(statistics.mean(e2e), ws, "cuda"))
     d2h = sum(len(o) * o.dtype.itemsize for o in outs) + 4 * 8 * 2 * len(imgs)
     code_h.free()
 
