@@ -591,3 +591,20 @@ def test_code_bits_flat_image_by_hand():
     bits = oracle.code_bits(stats, o_bits=7)
     assert bits == 320
     assert abs(oracle.compression_ratio(64, 64, bits) - 8 * 64 * 64 / 320) < 1e-12
+
+
+def test_psnr_and_u8_rounding_textbook_values():
+    """PSNR = 10 log10(255^2 / MSE): an error of 1 at every pixel gives MSE 1,
+    i.e. 20 log10 255 = 48.1308 dB; an error of 16 at one pixel of 256 gives
+    the same MSE; errors of 255 everywhere give 0 dB.  The decoder's final
+    rounding is half to even, clamped to [0, 255]."""
+    a = np.full((16, 16), 100, dtype=np.uint8)
+    b = a + 1
+    assert abs(oracle.psnr(a, b) - 48.13080360867909) < 1e-12
+    c = a.copy()
+    c[3, 5] = 116
+    assert abs(oracle.psnr(a, c) - 48.13080360867909) < 1e-12
+    assert oracle.psnr(np.zeros((4, 4), np.uint8), np.full((4, 4), 255, np.uint8)) == 0.0
+    assert oracle.psnr(a, b) == oracle.psnr(b, a)
+    v = np.array([0.5, 1.5, 2.5, -3.0, 300.0, 254.5, 254.6, -0.4])
+    np.testing.assert_array_equal(oracle.to_u8(v), [0, 2, 2, 0, 255, 254, 255, 0])
