@@ -223,7 +223,13 @@ int fic_encode(fic_ctx* ctx, const fic_image* imgs, int n_images, const fic_para
 /* fic_encode into an existing handle: the images must have the sizes (and
  * the host flag) and params must equal those `code` was created with; the
  * previous codes are overwritten and no device memory is allocated (the
- * handle's buffers are reused).  Returns FIC_EINVAL otherwise. */
+ * handle's buffers are reused).  Returns FIC_EINVAL otherwise.  With a
+ * non-NULL stream the first such call captures the device part of the
+ * encode into a CUDA graph held by `code`, and every call (that one
+ * included) launches the graph on `stream` after staging host images; the
+ * call returns without waiting for the encode (a copy from pageable host
+ * memory may block until the driver has staged it).  With a NULL stream the
+ * encode is enqueued kernel by kernel. */
 int fic_encode_again(fic_ctx* ctx, const fic_image* imgs, int n_images, const fic_params* params,
                      void* stream, fic_code* code);
 
