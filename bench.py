@@ -80,12 +80,13 @@ class Clocks:
 
     def __init__(self, index: int):
         self.index = index
+        self.gpu_id = gpu_identity(index)
         self.p = None
 
     def __enter__(self):
         try:
             self.p = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
@@ -115,7 +116,21 @@ class Clocks:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "gpu": self.gpu_id}
+
+
+def gpu_identity(index: int) -> str:
+    """nvidia-smi's name for the CUDA device `index`: its UUID (GPU-...), which
+    stays right when CUDA_VISIBLE_DEVICES renumbers the devices; the index
+    itself when torch cannot tell the UUID."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(index).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    return str(index)
 
 
 def _sm_max_mhz():

@@ -286,6 +286,26 @@ int fic_code_graph_kernels(const fic_code* code, int64_t* n_kernels);
 int fic_decode(fic_ctx* ctx, const fic_code* code, int image_idx, int max_iters, double tol,
                uint8_t* out, int out_pitch, int out_host, void* stream, int* iters_done);
 
+/* Test hook for the bounded device waits (the paper has no counterpart).
+ * Arms one fault for the next tensor-path matcher launch made through this
+ * context (fic_encode, fic_encode_again without graph replay, or
+ * fic_match_level); the launch disarms it.  0 disarms it without a launch.
+ *
+ *   FIC_FAULT_DROP_TILE_COPY  the copy engine is never asked for the first
+ *       domain tile of the first work item of CTA 0, so that tile's stage
+ *       never fills.  The waits on it give up after their limit (2 s), the
+ *       CTA abandons its remaining work, waits (also bounded) for the copies
+ *       it did issue, releases its tensor memory and returns; the call's
+ *       status becomes FIC_ETIMEOUT (reported by the handle's next
+ *       synchronising call), and the handle's results are not valid.  The
+ *       GPU is not faulted: the context and the handle stay usable, and the
+ *       next encode into the same handle starts from a clear status.
+ *
+ * Returns FIC_EINVAL for an unknown fault. */
+#define FIC_FAULT_NONE 0
+#define FIC_FAULT_DROP_TILE_COPY 1
+int fic_debug_inject(fic_ctx* ctx, int fault);
+
 /* Decoder that allocates no device memory.  The paper has no counterpart:
  * this is a deployment variant of fic_decode for callers that must not let a
  * library call cudaMalloc -- processes whose device memory belongs to another

@@ -44,8 +44,8 @@ void DevBuf::release() {
 struct fic_ctx {
   int device = 0;
   int nsm = 0;
-  DevBuf dT;      // entropy-key increments, kKeyTableN + 1 int64
-  DevBuf status;  // uint32 device status word
+  DevBuf dT;       // entropy-key increments, kKeyTableN + 1 int64
+  int inject = 0;  // fault armed for the next tensor matcher launch (fic_debug_inject)
 };
 
 namespace {
@@ -235,6 +235,7 @@ struct fic_code {
   DecodeWs dec;
   std::vector<int64_t> h_code_off[4];  // filled on first query
   std::vector<int64_t> h_rng_off;  // level-0 range offsets (host copy)
+  DevBuf status;                   // device status word of the last encode (kStatus*)
   cudaStream_t st = nullptr;       // stream of the last encode
   // replay of the device part of the encode (fic_encode_again)
   cudaGraphExec_t graph = nullptr;
@@ -251,6 +252,7 @@ struct fic_code {
 struct fic_pool {
   fic_ctx* ctx = nullptr;
   cudaStream_t st = nullptr;
+  DevBuf status;  // device status word (kStatus*)
   fic_params prm{};
   std::vector<fic_image> ims;
   Staging staging;
@@ -260,6 +262,7 @@ struct fic_pool {
 struct fic_matches {
   fic_ctx* ctx = nullptr;
   cudaStream_t st = nullptr;
+  DevBuf status;  // device status word (kStatus*)
   int64_t n = 0;
   LevelWs ws;
 };
@@ -329,8 +332,9 @@ int level_alloc(fic_ctx* ctx, LevelWs& w, const std::vector<fic_image>& ims, int
 // 1 on the last level, which accepts every range).  A pool built on another
 // stream joins through pool_ready, after the range operand and before the
 // plan, the first step that reads the pool.
-int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cudaStream_t st,
-                cudaEvent_t* ev = nullptr, int split = -1, cudaEvent_t pool_ready = nullptr) {
+int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, uint32_t* status,
+                cudaStream_t st, cudaEvent_t* ev = nullptr, int split = -1,
+                cudaEvent_t pool_ready = nullptr) {
   PoolLevel& pl = w.pool;
   const int ni = pl.n_images;
   const bool tc = prm.precision == FIC_PREC_TENSOR;
@@ -377,8 +381,14 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
   a.meta = w.meta.as<PlanMeta>();
   a.pm = PosMoments{pl.sd.as<int32_t>(), pl.sq.as<int32_t>(), pl.off.as<int64_t>()};
   a.part = w.part.as<Cand>();
-  a.status = ctx->status.as<uint32_t>();
-  auto match = [&]() { return tc ? launch_match_tc(a, grid, st) : launch_match_f32(a, grid, st); };
+  a.status = status;
+  // a fault armed by fic_debug_inject goes to the next tensor launch only
+  auto match = [&]() {
+    if (!tc) return launch_match_f32(a, grid, st);
+    a.inject = ctx->inject;
+    ctx->inject = 0;
+    return launch_match_tc(a, grid, st);
+  };
 
   // autotune: on the level's first eager run, time the matcher with a few
   // work-item counts per persistent CTA (every trial from freshly reset
@@ -429,7 +439,7 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, cuda
                              w.cap, w.act_off.as<int64_t>(), pl.slot_off.as<int64_t>(), ni, pl.L,
                              pl.sel.as<SelState>(), w.item_off.as<int64_t>(),
                              w.chunks.as<int32_t>(), w.part.as<Cand>(), tc ? 1 : 8, pl.sset, level,
-                             w.meta.as<PlanMeta>(), ctx->status.as<uint32_t>(),
+                             w.meta.as<PlanMeta>(), status,
                              w.res.as<fic_transform>(), prm.rms_threshold, split > 0 ? 1 : 0,
                              split >= 0 ? w.acc.as<uint8_t>() : nullptr, w.acc_cnt.as<int32_t>(),
                              w.rej_cnt.as<int32_t>(), tile_acc, a.pm, ctx->nsm, st);
@@ -468,6 +478,9 @@ int encode_device(fic_code* c, cudaStream_t st) {
   const int ni = c->n_images;
   const int B0 = prm.range_size0;
   int rc = FIC_OK;
+  // a fresh status for this encode (also a node of the captured graph, so
+  // every replay starts clear)
+  FIC_CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 16, st));
   // fork: every level's pool on its own side stream; each level joins its
   // pool before its plan, so level 0's ranges are set up meanwhile
   FIC_CUDA_TRY(cudaEventRecord(c->fork_ev, st));
@@ -488,8 +501,8 @@ int encode_device(fic_code* c, cudaStream_t st) {
                                           w.act_off.as<int64_t>(), w.act_cnt.as<int64_t>());
     }
     const bool last = (l == c->n_levels - 1);
-    if ((rc = level_match(ctx, w, prm, l, st, c->profile ? c->ev[l] : nullptr, last ? 1 : 0,
-                          c->pool_ev[l])))
+    if ((rc = level_match(ctx, w, prm, l, c->status.as<uint32_t>(), st,
+                          c->profile ? c->ev[l] : nullptr, last ? 1 : 0, c->pool_ev[l])))
       return rc;
     LevelWs* nx = last ? nullptr : &c->lv[l + 1];
     rc = launch_split(w.res.as<fic_transform>(), w.rec.as<RangeRec>(), w.n_act.as<int64_t>(), w.cap,
@@ -551,10 +564,11 @@ int encode_graph(fic_code* c, cudaStream_t st) {
   return FIC_OK;
 }
 
-int sync_and_status(fic_ctx* ctx, cudaStream_t st) {
+// Waits for `st` and reports the device status word of a handle.
+int sync_and_status(const DevBuf& status, cudaStream_t st) {
   FIC_CUDA_TRY(cudaStreamSynchronize(st));
   uint32_t s = 0;
-  FIC_CUDA_TRY(cudaMemcpy(&s, ctx->status.p, sizeof(s), cudaMemcpyDeviceToHost));
+  FIC_CUDA_TRY(cudaMemcpy(&s, status.p, sizeof(s), cudaMemcpyDeviceToHost));
   if (s & kStatusTimeout) return FIC_ETIMEOUT;
   if (s & kStatusOverflow) return FIC_ERANGE;
   return FIC_OK;
@@ -620,17 +634,14 @@ int fic_create(fic_ctx** out, int device) {
   }
   std::vector<int64_t> dT(kKeyTableN + 1);
   host_key_table(dT.data(), kKeyTableN);
-  if (c->dT.reserve(sizeof(int64_t) * dT.size()) || c->status.reserve(16)) {
+  if (c->dT.reserve(sizeof(int64_t) * dT.size())) {
     c->dT.release();
-    c->status.release();
     delete c;
     return FIC_ENOMEM;
   }
   if (cudaMemcpy(c->dT.p, dT.data(), sizeof(int64_t) * dT.size(), cudaMemcpyHostToDevice) !=
-          cudaSuccess ||
-      cudaMemset(c->status.p, 0, 16) != cudaSuccess) {
+      cudaSuccess) {
     c->dT.release();
-    c->status.release();
     delete c;
     return FIC_ECUDA;
   }
@@ -643,8 +654,13 @@ int fic_destroy(fic_ctx* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   c->dT.release();
-  c->status.release();
   delete c;
+  return FIC_OK;
+}
+
+int fic_debug_inject(fic_ctx* c, int fault) {
+  if (!c || (fault != FIC_FAULT_NONE && fault != FIC_FAULT_DROP_TILE_COPY)) return FIC_EINVAL;
+  c->inject = fault;
   return FIC_OK;
 }
 
@@ -664,7 +680,9 @@ int fic_build_domain_pool(fic_ctx* ctx, const fic_image* img, int range_size,
   p->st = st;
   p->prm = *params;
   p->ims = {*img};
-  int rc = p->staging.stage(p->ims, st);
+  int rc = p->status.reserve(16);
+  if (!rc && cudaMemsetAsync(p->status.p, 0, 16, st) != cudaSuccess) rc = FIC_ECUDA;
+  if (!rc) rc = p->staging.stage(p->ims, st);
   if (!rc) {
     std::vector<fic_image> dv = p->staging.device_view(p->ims);
     pool_geometry(p->pl, dv, range_size, params->domain_step);
@@ -688,7 +706,7 @@ int fic_build_domain_pool(fic_ctx* ctx, const fic_image* img, int range_size,
 
 int fic_pool_info(const fic_pool* p, fic_pool_info_t* out) {
   if (!p || !out) return FIC_EINVAL;
-  int rc = sync_and_status(p->ctx, p->st);
+  int rc = sync_and_status(p->status, p->st);
   if (rc) return rc;
   SelState s{};
   FIC_CUDA_TRY(cudaMemcpy(&s, p->pl.sel.p, sizeof(s), cudaMemcpyDeviceToHost));
@@ -706,7 +724,7 @@ int fic_pool_info(const fic_pool* p, fic_pool_info_t* out) {
 
 int fic_pool_copy(const fic_pool* p, int field, void* host_dst, size_t bytes) {
   if (!p || !host_dst) return FIC_EINVAL;
-  int rc = sync_and_status(p->ctx, p->st);
+  int rc = sync_and_status(p->status, p->st);
   if (rc) return rc;
   SelState s{};
   FIC_CUDA_TRY(cudaMemcpy(&s, p->pl.sel.p, sizeof(s), cudaMemcpyDeviceToHost));
@@ -750,6 +768,7 @@ void fic_pool_free(fic_pool* p) {
                    &pl.total, &pl.umax, &pl.run_off};
   for (DevBuf* b : all) b->release();
   p->staging.buf.release();
+  p->status.release();
   delete p;
 }
 
@@ -782,6 +801,8 @@ int fic_match_level(fic_ctx* ctx, const fic_image* img, const fic_pool* pool,
   std::vector<fic_image> ims = pool->staging.device_view(pool->ims);
   LevelWs& w = m->ws;
   int rc = level_alloc(ctx, w, ims, B, std::max(n_ranges, 1), *params);
+  if (!rc) rc = m->status.reserve(16);
+  if (!rc && cudaMemsetAsync(m->status.p, 0, 16, st) != cudaSuccess) rc = FIC_ECUDA;
   if (!rc) {
     // the level works on the pool's buffers; share them without copying
     w.pool = PoolLevel();
@@ -809,7 +830,7 @@ int fic_match_level(fic_ctx* ctx, const fic_image* img, const fic_pool* pool,
                 cudaMemcpyAsync(w.act_off.p, off, sizeof(off), cudaMemcpyHostToDevice, st) ||
                 cudaMemcpyAsync(w.act_cnt.p, &nact, sizeof(int64_t), cudaMemcpyHostToDevice, st)))
       rc = FIC_ECUDA;
-    if (!rc) rc = level_match(ctx, w, *params, 0, st);
+    if (!rc) rc = level_match(ctx, w, *params, 0, m->status.as<uint32_t>(), st);
     if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = FIC_ECUDA;  // host arrays above
   }
   // drop the borrowed buffers before any release
@@ -826,7 +847,7 @@ int fic_match_level(fic_ctx* ctx, const fic_image* img, const fic_pool* pool,
 
 int fic_matches_copy(const fic_matches* m, fic_match* host_out, size_t cap, size_t* count) {
   if (!m || (!host_out && cap > 0)) return FIC_EINVAL;
-  int rc = sync_and_status(m->ctx, m->st);
+  int rc = sync_and_status(m->status, m->st);
   if (rc) return rc;
   if (count) *count = (size_t)m->n;
   if (cap < (size_t)m->n) return FIC_ERANGE;
@@ -839,6 +860,7 @@ void fic_matches_free(fic_matches* m) {
   if (!m) return;
   cudaStreamSynchronize(m->st);
   m->ws.release_all();
+  m->status.release();
   delete m;
 }
 
@@ -851,6 +873,7 @@ static int code_setup(fic_ctx* ctx, const fic_image* imgs, int n_images, const f
   c->n_levels = params->single_level ? 1 : params->n_levels;
   c->ims.assign(imgs, imgs + n_images);
   c->dims = c->staging.device_view(c->ims);
+  if (c->status.reserve(16)) return FIC_ENOMEM;
   for (int l = 0; l < c->n_levels; ++l) {
     const int B = params->range_size0 >> l;
     LevelWs& w = c->lv[l];
@@ -950,7 +973,7 @@ int fic_code_graph_kernels(const fic_code* code, int64_t* n) {
 static int code_offsets(fic_code* c) {
   if (!c->h_code_off[0].empty()) return FIC_OK;
   FIC_CUDA_TRY(cudaDeviceSynchronize());
-  int rc = sync_and_status(c->ctx, nullptr);
+  int rc = sync_and_status(c->status, nullptr);
   if (rc) return rc;
   for (int l = 0; l < c->n_levels; ++l) {
     c->h_code_off[l].resize(c->n_images + 1);
@@ -1000,7 +1023,7 @@ int fic_code_stats(const fic_code* code, int image_idx, fic_level_stats* host_ou
   fic_code* c = const_cast<fic_code*>(code);
   cudaSetDevice(c->ctx->device);
   FIC_CUDA_TRY(cudaDeviceSynchronize());
-  int rc = sync_and_status(c->ctx, nullptr);
+  int rc = sync_and_status(c->status, nullptr);
   if (rc) return rc;
   for (int l = 0; l < c->n_levels; ++l) {
     const LevelWs& w = c->lv[l];
@@ -1078,6 +1101,7 @@ void fic_code_free(fic_code* c) {
   c->rng_off.release();
   c->staging.buf.release();
   c->dec.release();
+  c->status.release();
   delete c;
 }
 

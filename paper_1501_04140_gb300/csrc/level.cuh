@@ -52,7 +52,13 @@ struct MatchArgs {
                                     // or 16 ranges (tensor path)
   uint32_t* status;                 // device status word
   PosMoments pm;                    // the exact-s mode's V of a key
+  int inject;                       // test hook (kInjectDropTileCopy), 0 normally
 };
+
+// Test hook of the tensor matcher: the producer of CTA 0 leaves the first
+// stage of its first work item unfilled, so the waits on it run out after
+// kWaitLimitNs; the kernel then records kStatusTimeout and returns.
+constexpr int kInjectDropTileCopy = FIC_FAULT_DROP_TILE_COPY;
 
 int launch_range_pack(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
                       int64_t cap, int Kp, RangeMom* mom, uint32_t* gthr, uint16_t* apack,

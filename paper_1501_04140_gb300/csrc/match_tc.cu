@@ -327,6 +327,10 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
               ok = false;
               break;
             }
+            if (a.inject == kInjectDropTileCopy && blockIdx.x == 0 && si == 0) {
+              ++si;  // test hook: this stage is never filled (see MatchArgs::inject)
+              continue;
+            }
             ptx::mbar_expect_tx(&full_b[st], Cf::ST_BYTES);
             ptx::bulk_g2s(sB + st * Cf::ST_BYTES,
                           (const uint8_t*)a.bpack + (tile_g * Cf::NKC + kc) * Cf::ST_BYTES,

@@ -37,6 +37,14 @@ FIC_POOL_KEPT = 1
 FIC_POOL_SUMS = 2
 FIC_POOL_SQSUMS = 3
 
+# faults of the fic_debug_inject test hook
+FIC_FAULT_NONE = 0
+FIC_FAULT_DROP_TILE_COPY = 1
+
+# limits of fic_decode_static's fixed workspace
+FIC_DECODE_STATIC_MAX_PIXELS = 1024 * 1024
+FIC_DECODE_STATIC_MAX_ITERS = 1024
+
 
 class fic_params(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("range_size0", C.c_int), ("domain_step", C.c_int),
@@ -111,6 +119,7 @@ _SIGS = {
                              C.POINTER(C.c_int)]),
     "fic_decode_static": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_double, _P,
                                     C.c_int, _P, C.POINTER(C.c_int)]),
+    "fic_debug_inject": (C.c_int, [_P, C.c_int]),
 }
 
 _lib = None
@@ -200,10 +209,27 @@ def decode_static(codes_dev, n_codes: int, width: int, height: int, out_dev, out
                   max_iters: int = 300, tol: float = 1e-7, stream=None) -> int:
     """fic_decode_static: decode `n_codes` maps held in device memory at
     `codes_dev` (a pointer or a CUDA tensor) into the device buffer `out_dev`
-    without any device allocation.  Returns the iteration count."""
+    without any device allocation.  Returns the iteration count.
+
+    The library runs on the calling thread's current CUDA device and on the
+    given stream.  When `codes_dev` is a CUDA tensor the call makes its device
+    current for the call and, with no stream given, runs on torch's current
+    stream of that device, so work torch queued there (writing the codes or
+    the output buffer) is ordered before the decode.  With raw pointers the
+    caller sets the device and passes the stream (None: the legacy default
+    stream)."""
     it = C.c_int()
     cp = codes_dev.data_ptr() if hasattr(codes_dev, "data_ptr") else codes_dev
     op = out_dev.data_ptr() if hasattr(out_dev, "data_ptr") else out_dev
+    dev = getattr(codes_dev, "device", None)
+    if dev is not None and getattr(dev, "type", None) == "cuda":
+        import torch
+        with torch.cuda.device(dev):
+            st = stream if stream is not None else torch.cuda.current_stream(dev)
+            _check(load().fic_decode_static(cp, n_codes, width, height, max_iters, tol, op,
+                                            out_pitch, _stream_ptr(st), C.byref(it)),
+                   "fic_decode_static")
+        return it.value
     _check(load().fic_decode_static(cp, n_codes, width, height, max_iters, tol, op, out_pitch,
                                     _stream_ptr(stream), C.byref(it)), "fic_decode_static")
     return it.value
@@ -231,6 +257,11 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def debug_inject(self, fault: int):
+        """fic_debug_inject: arm a fault for the next tensor matcher launch
+        (test hook of the bounded device waits)."""
+        _check(load().fic_debug_inject(self._h, fault), "fic_debug_inject")
 
     # ---------------------------------------------------------------- pool
     def build_domain_pool(self, img, range_size: int, params: fic_params, stream=None) -> "Pool":

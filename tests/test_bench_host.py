@@ -25,6 +25,7 @@ def test_clock_summary_median_max_and_reasons():
     assert s["sm_max_mhz"] == 2070.0
     assert s["reasons"] == ["sw_power_cap"]
     assert s["samples"] == 5
+    assert s["gpu"] == bench.gpu_identity(0)
 
 
 def test_clock_summary_flags_every_slowdown_kind():
@@ -57,3 +58,22 @@ def test_peaks_measured_file_and_fallback(tmp_path, monkeypatch):
         '{"hbm_gbs": 7012.5, "bf16_tflops": 2101.0, "sm_max_mhz": 2062}')
     assert bench._peaks() == (7012.5, 2101.0, "measured")
     assert bench._sm_max_mhz() == 2062.0
+
+
+def test_gpu_identity_by_uuid(monkeypatch):
+    """The clock sampler names its GPU by UUID (CUDA_VISIBLE_DEVICES may
+    renumber devices, nvidia-smi's indices never change), falling back to the
+    index when torch cannot tell the UUID."""
+    import torch
+
+    class P:
+        uuid = "0a1b2c3d-0000-1111-2222-333344445555"
+
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda i: P())
+    assert bench.gpu_identity(0) == "GPU-0a1b2c3d-0000-1111-2222-333344445555"
+
+    def boom(i):
+        raise RuntimeError("no device")
+
+    monkeypatch.setattr(torch.cuda, "get_device_properties", boom)
+    assert bench.gpu_identity(3) == "3"

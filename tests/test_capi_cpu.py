@@ -59,3 +59,18 @@ def test_image_descriptor_host_and_pitch():
     a = np.zeros((32, 48), np.uint8)
     d, keep = fic.make_image(a)
     assert (d.width, d.height, d.pitch, d.host) == (48, 32, 48, 1)
+
+
+def test_binding_constants_match_header():
+    """Every FIC_* constant the binding defines has the value include/fic.h
+    gives it (status codes, modes, pool fields, the static decoder's limits)."""
+    import re
+    txt = open(fic.HEADER).read()
+    defs = dict(re.findall(r"#define (FIC_[A-Z0-9_]+) \(?([-0-9 *()]+?)\)?\s*(?:/\*|\n)", txt))
+    checked = 0
+    for name, expr in defs.items():
+        if hasattr(fic, name):
+            assert getattr(fic, name) == eval(expr, {}), name
+            checked += 1
+    assert checked >= 15
+    assert fic.FIC_DECODE_STATIC_MAX_PIXELS == 1024 * 1024

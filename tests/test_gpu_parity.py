@@ -347,37 +347,6 @@ def test_invalid_arguments():
     pool.free()
 
 
-# ------------------------------------------------------------- full size
-def test_paper_scale_sampled_parity():
-    """512 x 512, full quadtree, L = 2, predefined S (the headline workload):
-    every level's pool keys and kept list in full, and a sample of each
-    level's saved maps re-derived by the oracle's exhaustive search."""
-    fic = _fic()
-    ctx = G.ctx()
-    img = synth_image(512, 512, 1, n_textured=1)
-    p = fic.default_params()
-    code = ctx.encode(G.dev(img), p)
-    t = code.transforms(0)
-    st = code.stats(0)
-    rng = np.random.default_rng(0)
-    for lv in range(4):
-        B = 16 >> lv
-        keys_o, kept_o, thr_o, fb_o = oracle.pool_filter(img, B, 2, 0.5)
-        assert st[lv]["thr_key"] == thr_o and st[lv]["n_kept"] == len(kept_o)
-        rows = t[t["level"] == lv]
-        if len(rows) == 0:
-            continue
-        pick = rows[rng.choice(len(rows), size=min(6, len(rows)), replace=False)]
-        sp, q = oracle.s_set(0, 16, B)
-        ref = oracle.match(img, B, 2, kept_o, np.stack([pick["x"], pick["y"]], 1), sp, q,
-                           n_threads=8)
-        np.testing.assert_array_equal(pick["e_num"], ref["e_num"])
-        np.testing.assert_array_equal(G.keys_of(pick, len(sp)), ref["key"])
-    dec = code.decode(0)
-    assert oracle.psnr(img, dec) > 25.0
-    code.free()
-
-
 def test_graph_replay_and_profiling():
     """fic_encode_again on a stream captures the encode once and replays it:
     same maps as the direct encode; the level timers report positive times."""

@@ -57,6 +57,33 @@ def test_decode_static_equals_decode_on_two_calls():
     np.testing.assert_array_equal(out.cpu().numpy(), want)
 
 
+def test_decode_static_at_its_size_limits():
+    """The largest image the workspace takes (exactly its pixel maximum) and
+    the largest iteration count, with a tolerance of zero so that every
+    iteration runs: the last iterate and the last per-iteration maximum sit
+    at the far end of the workspace, and the image must still equal
+    fic_decode's with the same arguments byte for byte."""
+    ctx = G.ctx()
+    from paper_1501_04140_gb300 import fic
+    torch = G.torch_cuda()
+    side = int(round(fic.FIC_DECODE_STATIC_MAX_PIXELS ** 0.5))
+    assert side * side == fic.FIC_DECODE_STATIC_MAX_PIXELS
+    img = synth_image(side, side, 23, n_textured=2)
+    code = ctx.encode(G.dev(img), fic.default_params())
+    t = code.transforms(0)
+    iters_max = fic.FIC_DECODE_STATIC_MAX_ITERS
+    want = code.decode(0, max_iters=iters_max, tol=0.0)
+    assert code.iters == iters_max
+    code.free()
+    codes_dev = torch.from_numpy(t.view(np.uint8).copy()).cuda()
+    for _ in range(2):
+        out = torch.zeros((side, side), dtype=torch.uint8, device="cuda")
+        got = fic.decode_static(codes_dev, len(t), side, side, out, side, max_iters=iters_max,
+                                tol=0.0)
+        assert got == iters_max
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
 def test_decode_static_rejects_sizes_beyond_its_workspace():
     ctx = G.ctx()  # noqa: F841  (builds and loads the library)
     from paper_1501_04140_gb300 import fic
