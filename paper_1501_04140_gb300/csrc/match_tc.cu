@@ -755,8 +755,14 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           // current threshold (never looser than a valid bound); then the
           // accumulator goes back to the MMA.
           constexpr int CPW = Cf::NCH / Cf::GPT;  // chunks per warp
+          constexpr int NRW = CPW * RPC;          // ranges per warp and tile
           const int c0 = CPW * cp;
           float m = INFINITY;
+          // each range's margin stays in a register for the rare exact pass,
+          // which then visits only the ranges some lane of the warp flagged
+          float dm[NRW];
+#pragma unroll
+          for (int j = 0; j < NRW; ++j) dm[j] = INFINITY;
           if (ok) {
 #pragma unroll
             for (int h2 = 0; h2 < CPW; h2 += 2) {
@@ -778,7 +784,9 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
                   const float sa = score(cm[j], wv[j]), sb = score(cm[j + 1], wv[j + 1]);
-                  m = ptx::fmin3(m, sa - tv[j], sb - tv[j + 1]);
+                  dm[h2 * RPC + j] = sa - tv[j];
+                  dm[h2 * RPC + j + 1] = sb - tv[j + 1];
+                  m = ptx::fmin3(m, dm[h2 * RPC + j], dm[h2 * RPC + j + 1]);
                 }
               } else {
                 // two ranges per packed FMA: y = cmax - w sum Ds', the
@@ -794,6 +802,8 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
                     s2 = make_float2(fminf(s2.x, s1.x), fminf(s2.y, s1.y));
                   }
                   const float2 d2 = __fadd2_rn(s2, make_float2(-tv[j], -tv[j + 1]));
+                  dm[h2 * RPC + j] = d2.x;
+                  dm[h2 * RPC + j + 1] = d2.y;
                   m = ptx::fmin3(m, d2.x, d2.y);
                 }
               }
@@ -801,8 +811,16 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
           }
           if (__any_sync(0xffffffffu, dvalid && m <= 0.f)) {
             const DomRec dr = sDom[dl];
+            // the ranges that some lane's screen passed (a range no lane
+            // passed cannot pass now: thresholds only tighten, and a looser
+            // value left by a lost race is still a valid bound)
+            uint32_t fl = 0;
+#pragma unroll
+            for (int j = 0; j < NRW; ++j) fl |= (dvalid && dm[j] <= 0.f) ? 1u << j : 0u;
+            uint32_t wm = __reduce_or_sync(0xffffffffu, fl);
 #pragma unroll 1
-            for (int j = 0; j < CPW * RPC; ++j) {
+            for (; wm; wm &= wm - 1) {
+              const int j = __ffs(wm) - 1;
               const int r = c0 * RPC + j;
               float v[8];
               ptx::tmem_ld8_wait(tb + c0 * 32 + 8 * j, v);
