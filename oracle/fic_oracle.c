@@ -126,6 +126,11 @@ int oracle_pool_filter(const uint8_t* img, long pitch, int W, int H, int B, int 
   int nx, ny;
   int P = oracle_pool_size(W, H, B, L, &nx, &ny);
   if (P <= 0) return 0;
+  /* each position's key on its own (rows spread over the host's threads;
+   * every key is computed alone, in the same operations, in any order) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int iy = 0; iy < ny; ++iy)
     for (int ix = 0; ix < nx; ++ix)
       keys[iy * nx + ix] = oracle_entropy_key(img, pitch, ix * L, iy * L, 2 * B);
@@ -337,13 +342,16 @@ void oracle_match(const uint8_t* img, long pitch, int W, int H, int B, int L,
   int nx, ny;
   oracle_pool_size(W, H, B, L, &nx, &ny);
   const int n = B * B;
-  /* Decimated kept domains, computed once. */
+  /* Decimated kept domains, computed once (each on its own). */
   int64_t* Dall = (int64_t*)malloc(sizeof(int64_t) * (size_t)n * (size_t)(n_kept > 0 ? n_kept : 1));
+  if (n_threads < 1) n_threads = 1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(n_threads)
+#endif
   for (int j = 0; j < n_kept; ++j) {
     int d = kept[j];
     oracle_decimate(img, pitch, (d % nx) * L, (d / nx) * L, B, Dall + (size_t)j * n);
   }
-  if (n_threads < 1) n_threads = 1;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
 #endif

@@ -82,14 +82,18 @@ def _as_oracle_codes(maps):
     return out
 
 
-def _match_chunked(img, B, L, kept, rxy, sp, q, chunk=1 << 19):
+def _match_chunked(img, B, L, kept, rxy, sp, q, chunk=1 << 19, ex=None):
     """oracle.match over the whole kept pool, a bounded slice of the kept list
     at a time (the oracle decimates every kept domain of a call up front: a
-    4096^2 pool would hold 17 GB); the best of the slices' bests by (exact
-    error, tie-break key) is the best over the pool."""
+    4096^2 pool would hold 17 GB), the slices searched side by side when an
+    executor is given; the best of the slices' bests by (exact error,
+    tie-break key) is the best over the pool."""
+    def one(c0):
+        return oracle.match(img, B, L, kept[c0:c0 + chunk], rxy, sp, q, n_threads=NT)
+
+    starts = range(0, len(kept), chunk)
     best = None
-    for c0 in range(0, len(kept), chunk):
-        r = oracle.match(img, B, L, kept[c0:c0 + chunk], rxy, sp, q, n_threads=NT)
+    for r in (ex.map(one, starts) if ex is not None else map(one, starts)):
         if best is None:
             best = r
         else:
@@ -99,7 +103,7 @@ def _match_chunked(img, B, L, kept, rxy, sp, q, chunk=1 << 19):
     return best
 
 
-def _check_sampled_maps(img, t, lv, B, L, kept, n, rng, smode=0, M=16):
+def _check_sampled_maps(img, t, lv, B, L, kept, n, rng, smode=0, M=16, ex=None):
     """n saved maps of level lv re-derived by the oracle's exhaustive search
     over the level's kept pool: the exact error and the tie-break key equal."""
     rows = t[t["level"] == lv]
@@ -108,7 +112,7 @@ def _check_sampled_maps(img, t, lv, B, L, kept, n, rng, smode=0, M=16):
     pick = rows[rng.choice(len(rows), size=min(n, len(rows)), replace=False)]
     sp, q = oracle.s_set(smode, M, B)
     rxy = np.stack([pick["x"], pick["y"]], 1).astype(np.int32)
-    ref = _match_chunked(img, B, L, kept, rxy, sp, q)
+    ref = _match_chunked(img, B, L, kept, rxy, sp, q, ex=ex)
     np.testing.assert_array_equal(pick["e_num"], ref["e_num"])
     np.testing.assert_array_equal(G.keys_of(pick, len(sp)), ref["key"])
     return len(pick)
@@ -263,14 +267,20 @@ def test_4096_full_pool_sampled():
     code.free()
     n_pick = {0: 6, 1: 6, 2: 16, 3: 16}
 
-    def level(lv):
-        B = 16 >> lv
-        _, kept, thr, fb = oracle.pool_filter(img, B, 1, 0.5)
-        assert st[lv]["pool_size"] == oracle.pool_size(4096, 4096, B, 1)[0]
-        assert (st[lv]["thr_key"], st[lv]["n_kept"], st[lv]["fallback"]) == (thr, len(kept), fb)
-        return _check_sampled_maps(img, t, lv, B, 1, kept, n_pick[lv],
-                                   np.random.default_rng(11 + lv))
+    def pool(lv):
+        return oracle.pool_filter(img, 16 >> lv, 1, 0.5)
 
+    # the four pool filters side by side, then each level's search with its
+    # domain slices side by side (8 at a time: a slice holds up to 1 GB)
     with cf.ThreadPoolExecutor(max_workers=4) as ex:
-        checked = list(ex.map(level, range(4)))
+        pools = list(ex.map(pool, range(4)))
+    checked = []
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:
+        for lv, (_, kept, thr, fb) in enumerate(pools):
+            B = 16 >> lv
+            assert st[lv]["pool_size"] == oracle.pool_size(4096, 4096, B, 1)[0]
+            assert (st[lv]["thr_key"], st[lv]["n_kept"], st[lv]["fallback"]) == (thr, len(kept),
+                                                                                  fb)
+            checked.append(_check_sampled_maps(img, t, lv, B, 1, kept, n_pick[lv],
+                                               np.random.default_rng(11 + lv), ex=ex))
     assert all(c > 0 for c in checked), checked
