@@ -87,10 +87,16 @@ typedef struct {
   double entropy_percentile; /* threshold = pool entropy at this percentile    */
   int precision;             /* FIC_PREC_TENSOR or FIC_PREC_FP32               */
   int autotune;              /* 0: the default schedule (4 work items per
-                                persistent CTA); 1: on a level's first eager
-                                run, time the matcher with 2, 3, 4, 6 and 8
-                                items per CTA and keep the fastest for the
-                                code's later encodes (results are unchanged) */
+                                persistent CTA; on the tensor path one
+                                epilogue warp group per tile at B <= 4, two at
+                                B = 8); 1: on a level's first eager run, time
+                                the matcher with 2, 3, 4, 6 and 8 items per
+                                CTA and, on the tensor path at B <= 8, one or
+                                two epilogue groups per tile (8 or 16 ranges
+                                per warp visit), each schedule the median of
+                                5 launches, and keep the fastest for the
+                                code's later encodes (results are unchanged;
+                                fic_code_schedule reports the choice)        */
   int pool_size;             /* K > 0: the entropy filter keeps the K domains
                                 of highest entropy (Tables 1-2's "pool size":
                                 threshold = the (K+1)-th highest entropy, kept
@@ -233,11 +239,16 @@ int fic_encode(fic_ctx* ctx, const fic_image* imgs, int n_images, const fic_para
 int fic_encode_again(fic_ctx* ctx, const fic_image* imgs, int n_images, const fic_params* params,
                      void* stream, fic_code* code);
 
-/* Number of codes of image `image_idx` (synchronises). */
+/* Number of codes of image `image_idx`.  The first query after an encode
+ * waits for the encode's stream and reads back, in one copy, the code
+ * offsets of every image and level together with the encode's status
+ * (FIC_ETIMEOUT / FIC_ERANGE are reported here); later queries use them. */
 int fic_code_count(const fic_code* code, int image_idx, size_t* count);
 
-/* Copy the codes of one image to host, level-major then in range order
- * (synchronises).  Fails with FIC_ERANGE when cap is too small. */
+/* Copy the codes of one image to host, level-major then in range order:
+ * one asynchronous copy per level on the encode's stream and one wait
+ * (page-locked host_out is written by DMA directly).  Fails with FIC_ERANGE
+ * when cap is too small. */
 int fic_code_get(const fic_code* code, int image_idx, fic_transform* host_out, size_t cap,
                  size_t* count);
 
@@ -272,6 +283,16 @@ void fic_code_free(fic_code* code);
  * profiling on or off discards a captured graph. */
 int fic_code_set_profiling(fic_code* code, int on);
 int fic_code_profile(const fic_code* code, float* ms, int cap);
+/* With profiling on: per level, the ms of the level's pool build (Sec. 3:
+ * entropy keys, threshold, kept list, packed operand), timed on the side
+ * stream it runs on (cap >= n_levels floats; synchronises). */
+int fic_code_pool_profile(const fic_code* code, float* ms, int cap);
+
+/* The matcher schedule of every level of `code` (the default, or the
+ * autotuner's choice once a level has been tuned): 2 ints per level, {work
+ * items per persistent CTA, epilogue warp groups per tile}; cap >= 2 *
+ * n_levels. */
+int fic_code_schedule(const fic_code* code, int32_t* out, int cap);
 
 /* Kernels in the graph that fic_encode_again replays (captured on its first
  * call with a non-NULL stream); -1 before that. */

@@ -61,7 +61,8 @@ struct LevelWs {
   DevBuf item_off, chunks, meta, part;
   int64_t item_cap = 0, mt_cap = 0;
   int items_per_cta = 4;                   // the plan's work items per persistent CTA
-  bool tuned = false;                      // items_per_cta chosen by timing (autotune)
+  int groups_per_tile = 2;                 // tensor matcher, B <= 8: epilogue groups per tile
+  bool tuned = false;                      // both chosen by timing (autotune)
   DevBuf scan_scr, total;
   void release_all() {
     DevBuf* all[] = {&pool.off,  &pool.img,   &pool.keys,   &pool.sd,    &pool.sq,     &pool.sel,
@@ -126,17 +127,28 @@ int pool_alloc(PoolLevel& pl) {
   return rc ? FIC_ENOMEM : FIC_OK;
 }
 
-int pool_upload(PoolLevel& pl, const std::vector<const uint8_t*>& dev_pix, cudaStream_t st) {
-  for (int i = 0; i < pl.n_images; ++i) pl.h_img[i].pix = dev_pix[i];
+// The pool's size tables (fixed by the image sizes) ...
+int pool_upload_sizes(PoolLevel& pl, cudaStream_t st) {
   FIC_CUDA_TRY(cudaMemcpyAsync(pl.off.p, pl.h_off.data(), sizeof(int64_t) * (pl.n_images + 1),
                                cudaMemcpyHostToDevice, st));
   FIC_CUDA_TRY(cudaMemcpyAsync(pl.slot_off.p, pl.h_slot_off.data(),
                                sizeof(int64_t) * (pl.n_images + 1), cudaMemcpyHostToDevice, st));
-  FIC_CUDA_TRY(cudaMemcpyAsync(pl.img.p, pl.h_img.data(), sizeof(ImgDev) * pl.n_images,
-                               cudaMemcpyHostToDevice, st));
   FIC_CUDA_TRY(cudaMemcpyAsync(pl.run_off.p, pl.h_run_off.data(),
                                sizeof(int64_t) * (pl.n_images + 1), cudaMemcpyHostToDevice, st));
   return FIC_OK;
+}
+
+// ... and the image descriptors (device pointers of the images)
+int pool_upload_images(PoolLevel& pl, const std::vector<const uint8_t*>& dev_pix, cudaStream_t st) {
+  for (int i = 0; i < pl.n_images; ++i) pl.h_img[i].pix = dev_pix[i];
+  FIC_CUDA_TRY(cudaMemcpyAsync(pl.img.p, pl.h_img.data(), sizeof(ImgDev) * pl.n_images,
+                               cudaMemcpyHostToDevice, st));
+  return FIC_OK;
+}
+
+int pool_upload(PoolLevel& pl, const std::vector<const uint8_t*>& dev_pix, cudaStream_t st) {
+  int rc = pool_upload_sizes(pl, st);
+  return rc ? rc : pool_upload_images(pl, dev_pix, st);
 }
 
 bool valid_image(const fic_image& im, int B0) {
@@ -202,6 +214,7 @@ __global__ void k_init_ranges(const int64_t* __restrict__ rng_off, int n_images,
                               const ImgDev* __restrict__ imgs, int B, RangeRec* __restrict__ rec,
                               int64_t* __restrict__ n_act, int64_t* __restrict__ act_off,
                               int64_t* __restrict__ act_cnt) {
+  grid_dep_sync();
   const int64_t N = rng_off[n_images];
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -235,14 +248,24 @@ struct fic_code {
   DecodeWs dec;
   std::vector<int64_t> h_code_off[4];  // filled on first query
   std::vector<int64_t> h_rng_off;  // level-0 range offsets (host copy)
-  DevBuf status;                   // device status word of the last encode (kStatus*)
+  // Read-back summary, one allocation: the code offsets of every level
+  // (n_levels x (n_images + 1) int64; each level's code_off aliases its
+  // slice) followed by the device status word of the last encode, so one
+  // copy brings back everything a read of the codes needs first.
+  DevBuf summary;
+  DevBuf status;                   // alias of the summary's status word
   cudaStream_t st = nullptr;       // stream of the last encode
+  // what the device holds of the host-side tables: the size tables are
+  // uploaded once, the image descriptors when an image pointer changes
+  bool sizes_up = false;
+  std::vector<const uint8_t*> dev_pix_up;
   // replay of the device part of the encode (fic_encode_again)
   cudaGraphExec_t graph = nullptr;
   int64_t graph_kernels = 0;
   // optional per-level events around the matcher and the whole level
   bool profile = false;
   cudaEvent_t ev[4][4] = {};
+  cudaEvent_t pev[4][2] = {};  // each level's pool build, on its side stream
   // the pools of levels 1.. depend on the images only: they are built on
   // side streams forked from the encode's stream, off the level chain
   cudaStream_t side[4] = {};
@@ -288,6 +311,9 @@ int level_alloc(fic_ctx* ctx, LevelWs& w, const std::vector<fic_image>& ims, int
   w.n = B * B;
   w.Kp = kp_of(B);
   w.cap = cap;
+  // default shape (measured on a 512 x 512 encode): one epilogue group per
+  // tile (16 ranges per warp visit) at B <= 4, two at B = 8
+  w.groups_per_tile = B <= 4 ? 1 : 2;
   const int64_t C = cap + kTileRanges;  // one spare M tile
   const bool tc = prm.precision == FIC_PREC_TENSOR;
   int rc = 0;
@@ -349,12 +375,13 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, uint
                                tc ? nullptr : w.a32.as<float>(), ctx->nsm, st);
     if (rc) return rc;
     if (pool_ready) FIC_CUDA_TRY(cudaStreamWaitEvent(st, pool_ready, 0));
-    k_plan<<<1, 256, 0, st>>>(ni, w.act_off.as<int64_t>(), w.act_cnt.as<int64_t>(),
-                              pl.sel.as<SelState>(), items_per_cta * grid, w.item_cap, w.mt_cap,
-                              w.meta.as<PlanMeta>(), w.item_off.as<int64_t>(),
-                              w.chunks.as<int32_t>(), w.acc_cnt.as<int32_t>(),
-                              w.rej_cnt.as<int32_t>(), tile_acc, n_tiles);
-    return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
+    const cudaError_t e = launch_dep(
+        k_plan, dim3(1), dim3(256), 0, st, ni, (const int64_t*)w.act_off.as<int64_t>(),
+        (const int64_t*)w.act_cnt.as<int64_t>(), (const SelState*)pl.sel.as<SelState>(),
+        items_per_cta * grid, w.item_cap, w.mt_cap, w.meta.as<PlanMeta>(),
+        w.item_off.as<int64_t>(), w.chunks.as<int32_t>(), w.acc_cnt.as<int32_t>(),
+        w.rej_cnt.as<int32_t>(), tile_acc, n_tiles);
+    return e == cudaSuccess ? FIC_OK : FIC_ECUDA;
   };
   MatchArgs a{};
   a.B = w.B;
@@ -381,6 +408,7 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, uint
   a.meta = w.meta.as<PlanMeta>();
   a.pm = PosMoments{pl.sd.as<int32_t>(), pl.sq.as<int32_t>(), pl.off.as<int64_t>()};
   a.part = w.part.as<Cand>();
+  a.groups_per_tile = w.groups_per_tile;
   a.status = status;
   // a fault armed by fic_debug_inject goes to the next tensor launch only
   auto match = [&]() {
@@ -390,42 +418,59 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, uint
     return launch_match_tc(a, grid, st);
   };
 
-  // autotune: on the level's first eager run, time the matcher with a few
-  // work-item counts per persistent CTA (every trial from freshly reset
-  // thresholds) and keep the fastest for the level's later encodes and the
+  // autotune: on the level's first eager run, time the matcher over a grid
+  // of schedules -- work items per persistent CTA, and at B <= 8 on the
+  // tensor path the epilogue groups per tile (two groups with 8 ranges per
+  // warp visit, or one with 16) -- each candidate from freshly reset
+  // thresholds, one untimed launch and then the median of kTrials timed
+  // ones, and keep the fastest for the level's later encodes and the
   // captured graph
   if (prm.autotune && !w.tuned) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     FIC_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
     if (cs == cudaStreamCaptureStatusNone) {
-      static const int kCand[] = {2, 3, 4, 6, 8};
+      static const int kItems[] = {2, 3, 4, 6, 8};
+      constexpr int kTrials = 5;
+      const int n_groups = (tc && w.B <= 8) ? 2 : 1;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       int rc = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess
                    ? FIC_OK
                    : FIC_ECUDA;
-      // one untimed launch first: a kernel's first launch carries one-time
-      // costs (module loading) that would count against the first trial
-      if (!rc) rc = pack_plan(kCand[0]);
-      if (!rc) rc = match();
       float best = INFINITY;
-      for (int cand : kCand) {
-        if (rc) break;
-        if ((rc = pack_plan(cand))) break;
-        float ms = 0.f;
-        if (cudaEventRecord(e0, st) != cudaSuccess || (rc = match()) ||
-            cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-          rc = rc ? rc : FIC_ECUDA;
-          break;
-        }
-        if (ms < best) {
-          best = ms;
-          w.items_per_cta = cand;
+      int best_items = w.items_per_cta, best_groups = w.groups_per_tile;
+      for (int gi = 0; !rc && gi < n_groups; ++gi) {
+        a.groups_per_tile = n_groups == 1 ? w.groups_per_tile : 2 - gi;
+        for (int cand : kItems) {
+          if (rc) break;
+          float ms[kTrials];
+          // one untimed launch: a kernel's first launch carries one-time
+          // costs (module loading) that would count against the candidate
+          for (int t = -1; !rc && t < kTrials; ++t) {
+            if ((rc = pack_plan(cand))) break;
+            if (t < 0) {
+              rc = match();
+              continue;
+            }
+            if (cudaEventRecord(e0, st) != cudaSuccess || (rc = match()) ||
+                cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms[t], e0, e1) != cudaSuccess)
+              rc = rc ? rc : FIC_ECUDA;
+          }
+          if (rc) break;
+          std::sort(ms, ms + kTrials);
+          if (ms[kTrials / 2] < best) {
+            best = ms[kTrials / 2];
+            best_items = cand;
+            best_groups = a.groups_per_tile;
+          }
         }
       }
       if (e0) cudaEventDestroy(e0);
       if (e1) cudaEventDestroy(e1);
       if (rc) return rc;
+      w.items_per_cta = best_items;
+      w.groups_per_tile = best_groups;
+      a.groups_per_tile = best_groups;
       w.tuned = true;
     }
   }
@@ -459,16 +504,24 @@ int encode_upload(fic_code* c, cudaStream_t st) {
   const int ni = c->n_images;
   int rc = c->staging.stage(c->ims, st);
   if (rc) return rc;
-  const int B0 = c->prm.range_size0;
-  std::vector<int64_t>& roff = c->h_rng_off;
-  roff.assign(ni + 1, 0);
-  for (int i = 0; i < ni; ++i)
-    roff[i + 1] = roff[i] + (int64_t)(c->dims[i].width / B0) * (c->dims[i].height / B0);
-  if (c->rng_off.reserve(sizeof(int64_t) * (ni + 1))) return FIC_ENOMEM;
-  FIC_CUDA_TRY(cudaMemcpyAsync(c->rng_off.p, roff.data(), sizeof(int64_t) * (ni + 1),
-                               cudaMemcpyHostToDevice, st));
-  for (int l = 0; l < c->n_levels; ++l)
-    if ((rc = pool_upload(c->lv[l].pool, c->staging.dev_pix, st))) return rc;
+  if (!c->sizes_up) {
+    const int B0 = c->prm.range_size0;
+    std::vector<int64_t>& roff = c->h_rng_off;
+    roff.assign(ni + 1, 0);
+    for (int i = 0; i < ni; ++i)
+      roff[i + 1] = roff[i] + (int64_t)(c->dims[i].width / B0) * (c->dims[i].height / B0);
+    if (c->rng_off.reserve(sizeof(int64_t) * (ni + 1))) return FIC_ENOMEM;
+    FIC_CUDA_TRY(cudaMemcpyAsync(c->rng_off.p, roff.data(), sizeof(int64_t) * (ni + 1),
+                                 cudaMemcpyHostToDevice, st));
+    for (int l = 0; l < c->n_levels; ++l)
+      if ((rc = pool_upload_sizes(c->lv[l].pool, st))) return rc;
+    c->sizes_up = true;
+  }
+  if (c->dev_pix_up != c->staging.dev_pix) {
+    for (int l = 0; l < c->n_levels; ++l)
+      if ((rc = pool_upload_images(c->lv[l].pool, c->staging.dev_pix, st))) return rc;
+    c->dev_pix_up = c->staging.dev_pix;
+  }
   return FIC_OK;
 }
 
@@ -486,7 +539,9 @@ int encode_device(fic_code* c, cudaStream_t st) {
   FIC_CUDA_TRY(cudaEventRecord(c->fork_ev, st));
   for (int l = 0; l < c->n_levels; ++l) {
     FIC_CUDA_TRY(cudaStreamWaitEvent(c->side[l], c->fork_ev, 0));
+    if (c->profile) FIC_CUDA_TRY(record_event(c->pev[l][0], c->side[l]));
     if ((rc = pool_build(c->lv[l].pool, ctx->dT.as<int64_t>(), c->side[l]))) return rc;
+    if (c->profile) FIC_CUDA_TRY(record_event(c->pev[l][1], c->side[l]));
     FIC_CUDA_TRY(cudaEventRecord(c->pool_ev[l], c->side[l]));
   }
   for (int l = 0; l < c->n_levels; ++l) {
@@ -496,9 +551,11 @@ int encode_device(fic_code* c, cudaStream_t st) {
     if (l == 0) {
       const int64_t nr = c->h_rng_off[ni];
       const int grid = (int)std::min<int64_t>(65535, ceil_div64(std::max<int64_t>(nr, 1), 256));
-      k_init_ranges<<<grid, 256, 0, st>>>(c->rng_off.as<int64_t>(), ni, pl.img.as<ImgDev>(), B0,
-                                          w.rec.as<RangeRec>(), w.n_act.as<int64_t>(),
-                                          w.act_off.as<int64_t>(), w.act_cnt.as<int64_t>());
+      FIC_CUDA_TRY(launch_dep(k_init_ranges, dim3(grid), dim3(256), 0, st,
+                              (const int64_t*)c->rng_off.as<int64_t>(), ni,
+                              (const ImgDev*)pl.img.as<ImgDev>(), B0, w.rec.as<RangeRec>(),
+                              w.n_act.as<int64_t>(), w.act_off.as<int64_t>(),
+                              w.act_cnt.as<int64_t>()));
     }
     const bool last = (l == c->n_levels - 1);
     if ((rc = level_match(ctx, w, prm, l, c->status.as<uint32_t>(), st,
@@ -873,7 +930,10 @@ static int code_setup(fic_ctx* ctx, const fic_image* imgs, int n_images, const f
   c->n_levels = params->single_level ? 1 : params->n_levels;
   c->ims.assign(imgs, imgs + n_images);
   c->dims = c->staging.device_view(c->ims);
-  if (c->status.reserve(16)) return FIC_ENOMEM;
+  const size_t off_bytes = sizeof(int64_t) * 4 * (size_t)(n_images + 1);
+  if (c->summary.reserve(off_bytes + 16)) return FIC_ENOMEM;
+  c->status.p = (uint8_t*)c->summary.p + off_bytes;
+  c->status.bytes = 16;
   for (int l = 0; l < c->n_levels; ++l) {
     const int B = params->range_size0 >> l;
     LevelWs& w = c->lv[l];
@@ -882,6 +942,9 @@ static int code_setup(fic_ctx* ctx, const fic_image* imgs, int n_images, const f
     int rc = level_alloc(ctx, w, c->dims, B, ranges_at(c->dims, B), *params);
     if (!rc) rc = pool_alloc(w.pool);
     if (rc) return rc;
+    w.code_off.release();  // the level's offsets live in the summary
+    w.code_off.p = c->summary.as<int64_t>() + (size_t)l * (n_images + 1);
+    w.code_off.bytes = sizeof(int64_t) * (size_t)(n_images + 1);
     // level 0's pool is on the critical path: the greatest priority; the
     // later levels' pools the least, so the level chain's kernels go first
     int lo = 0, hi = 0;
@@ -942,9 +1005,12 @@ int fic_encode_again(fic_ctx* ctx, const fic_image* imgs, int n_images, const fi
 int fic_code_set_profiling(fic_code* code, int on) {
   if (!code) return FIC_EINVAL;
   cudaSetDevice(code->ctx->device);
-  if (on && !code->ev[0][0])
+  if (on && !code->ev[0][0]) {
     for (auto& lv : code->ev)
       for (auto& e : lv) FIC_CUDA_TRY(cudaEventCreate(&e));
+    for (auto& lv : code->pev)
+      for (auto& e : lv) FIC_CUDA_TRY(cudaEventCreate(&e));
+  }
   if ((on != 0) != code->profile && code->graph) {  // the graph holds the old choice
     cudaGraphExecDestroy(code->graph);
     code->graph = nullptr;
@@ -964,22 +1030,44 @@ int fic_code_profile(const fic_code* code, float* ms, int cap) {
   return FIC_OK;
 }
 
+int fic_code_pool_profile(const fic_code* code, float* ms, int cap) {
+  if (!code || !ms || cap < code->n_levels) return FIC_EINVAL;
+  if (!code->profile) return FIC_EINVAL;
+  FIC_CUDA_TRY(cudaStreamSynchronize(code->st));
+  for (int l = 0; l < code->n_levels; ++l)
+    FIC_CUDA_TRY(cudaEventElapsedTime(&ms[l], code->pev[l][0], code->pev[l][1]));
+  return FIC_OK;
+}
+
+int fic_code_schedule(const fic_code* code, int32_t* out, int cap) {
+  if (!code || !out || cap < 2 * code->n_levels) return FIC_EINVAL;
+  for (int l = 0; l < code->n_levels; ++l) {
+    out[2 * l] = code->lv[l].items_per_cta;
+    out[2 * l + 1] = code->lv[l].groups_per_tile;
+  }
+  return FIC_OK;
+}
+
 int fic_code_graph_kernels(const fic_code* code, int64_t* n) {
   if (!code || !n) return FIC_EINVAL;
   *n = code->graph ? code->graph_kernels : -1;
   return FIC_OK;
 }
 
+// The code offsets of every level and the status of the last encode, in one
+// copy after the encode's stream has finished (cached until the next encode).
 static int code_offsets(fic_code* c) {
   if (!c->h_code_off[0].empty()) return FIC_OK;
-  FIC_CUDA_TRY(cudaDeviceSynchronize());
-  int rc = sync_and_status(c->status, nullptr);
-  if (rc) return rc;
-  for (int l = 0; l < c->n_levels; ++l) {
-    c->h_code_off[l].resize(c->n_images + 1);
-    FIC_CUDA_TRY(cudaMemcpy(c->h_code_off[l].data(), c->lv[l].code_off.p,
-                            sizeof(int64_t) * (c->n_images + 1), cudaMemcpyDeviceToHost));
-  }
+  FIC_CUDA_TRY(cudaStreamSynchronize(c->st));
+  const size_t per = (size_t)c->n_images + 1;
+  std::vector<int64_t> h(4 * per + 2);
+  FIC_CUDA_TRY(cudaMemcpy(h.data(), c->summary.p, c->summary.bytes, cudaMemcpyDeviceToHost));
+  uint32_t s = 0;
+  memcpy(&s, &h[4 * per], sizeof(s));
+  if (s & kStatusTimeout) return FIC_ETIMEOUT;
+  if (s & kStatusOverflow) return FIC_ERANGE;
+  for (int l = 0; l < c->n_levels; ++l)
+    c->h_code_off[l].assign(h.begin() + l * per, h.begin() + (l + 1) * per);
   return FIC_OK;
 }
 
@@ -987,7 +1075,6 @@ int fic_code_count(const fic_code* code, int image_idx, size_t* count) {
   if (!code || !count || image_idx < 0 || image_idx >= code->n_images) return FIC_EINVAL;
   fic_code* c = const_cast<fic_code*>(code);
   cudaSetDevice(c->ctx->device);
-  FIC_CUDA_TRY(cudaDeviceSynchronize());
   int rc = code_offsets(c);
   if (rc) return rc;
   size_t s = 0;
@@ -1006,14 +1093,18 @@ int fic_code_get(const fic_code* code, int image_idx, fic_transform* host_out, s
   if (cap < total) return FIC_ERANGE;
   if (total && !host_out) return FIC_EINVAL;
   fic_code* c = const_cast<fic_code*>(code);
+  // one asynchronous copy per level on the encode's stream, one wait (the
+  // copies run as DMA straight into host_out when it is page-locked)
   size_t o = 0;
   for (int l = 0; l < c->n_levels; ++l) {
     const int64_t a = c->h_code_off[l][image_idx], b = c->h_code_off[l][image_idx + 1];
     if (b > a)
-      FIC_CUDA_TRY(cudaMemcpy(host_out + o, c->lv[l].codes.as<fic_transform>() + a,
-                              sizeof(fic_transform) * (size_t)(b - a), cudaMemcpyDeviceToHost));
+      FIC_CUDA_TRY(cudaMemcpyAsync(host_out + o, c->lv[l].codes.as<fic_transform>() + a,
+                                   sizeof(fic_transform) * (size_t)(b - a),
+                                   cudaMemcpyDeviceToHost, c->st));
     o += (size_t)(b - a);
   }
+  FIC_CUDA_TRY(cudaStreamSynchronize(c->st));
   return FIC_OK;
 }
 
@@ -1092,16 +1183,25 @@ void fic_code_free(fic_code* c) {
   for (auto& lv : c->ev)
     for (auto& e : lv)
       if (e) cudaEventDestroy(e);
+  for (auto& lv : c->pev)
+    for (auto& e : lv)
+      if (e) cudaEventDestroy(e);
   for (int l = 0; l < 4; ++l) {
     if (c->pool_ev[l]) cudaEventDestroy(c->pool_ev[l]);
     if (c->side[l]) cudaStreamDestroy(c->side[l]);
   }
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  for (auto& w : c->lv) {  // a level's offsets alias the summary once set up
+    const uint8_t* q = (const uint8_t*)w.code_off.p;
+    const uint8_t* b = (const uint8_t*)c->summary.p;
+    if (q && b && q >= b && q < b + c->summary.bytes) w.code_off = DevBuf();
+  }
   for (auto& w : c->lv) w.release_all();
   c->rng_off.release();
   c->staging.buf.release();
   c->dec.release();
-  c->status.release();
+  c->status = DevBuf();  // alias of the summary
+  c->summary.release();
   delete c;
 }
 
@@ -1147,11 +1247,13 @@ int fic_decode(fic_ctx* ctx, const fic_code* code, int image_idx, int max_iters,
       cudaMemcpy2DAsync(out, out_pitch, dptr, W, W, H, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     rc = FIC_ECUDA;
   if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = FIC_ECUDA;
-  if (!rc && iters_done) {
-    int32_t ctl[2];
+  if (!rc) {
+    int32_t ctl[4];  // done, iterations, a barrier wait that ran out
     if (cudaMemcpy(ctl, c->dec.ctl.p, sizeof(ctl), cudaMemcpyDeviceToHost) != cudaSuccess)
       rc = FIC_ECUDA;
-    else
+    else if (ctl[2])
+      rc = FIC_ETIMEOUT;
+    else if (iters_done)
       *iters_done = ctl[1];
   }
   gathered.release();

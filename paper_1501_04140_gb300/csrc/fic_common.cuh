@@ -109,6 +109,20 @@ __host__ __device__ inline bool exact_better(int64_t Ca, int64_t Va, int64_t ka,
   return l > r || (l == r && ka < kb);
 }
 
+// ---------------------------------------------------------------- launches
+// Programmatic dependent launch.  The kernels of the level chain and of the
+// pool builds are launched with programmatic stream serialisation
+// (launch_dep), so the next kernel of a stream is launched -- its blocks
+// placed on the SMs -- while the previous one is still running; each such
+// kernel starts with grid_dep_sync(), which waits until the kernels before it
+// on the stream have completed and their writes are visible, and then lets
+// the kernel after it be launched in turn.  Without a programmatic
+// predecessor the wait returns at once.
+__device__ __forceinline__ void grid_dep_sync() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- helpers
 __host__ __device__ inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }

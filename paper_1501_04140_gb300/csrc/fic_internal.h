@@ -11,6 +11,37 @@
 
 namespace fic {
 
+// A kernel launch with programmatic stream serialisation (see
+// grid_dep_sync): the kernel must begin with grid_dep_sync().
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
+}
+
+// The same launch without programmatic serialisation (the kernel's
+// grid_dep_sync() then returns at once).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_std(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  return cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
+}
+
 // Device buffer owned by a plan; grows, never shrinks.
 struct DevBuf {
   void* p = nullptr;

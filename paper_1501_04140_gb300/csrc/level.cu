@@ -56,6 +56,7 @@ k_range_pack(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec,
   constexpr int n = B * B;
   constexpr int RPB = kRangePackThreads / n;  // ranges per block step
   __shared__ int s_sr[RPB], s_s2[RPB], s_sa[RPB];
+  grid_dep_sync();
   const int64_t N = *n_act;
   const int lr = threadIdx.x / n, e = threadIdx.x % n;
   const int i = e / B, j = e % B;
@@ -108,14 +109,18 @@ int launch_range_pack(int B, const ImgDev* imgs, const RangeRec* rec, const int6
   // grid-stride over the device count: at most 8 resident blocks per SM
   const int64_t gmax = nsm > 0 ? 8 * (int64_t)nsm : 65535;
   const int grid = (int)std::min<int64_t>(ceil_div64(cap > 0 ? cap : 1, rpb), gmax);
+  cudaError_t e;
+#define FIC_RP(BB) launch_dep(k_range_pack<BB>, dim3(grid), dim3(threads), 0, st, imgs, rec, n_act, \
+                              Kp, mom, gthr, apack, a32)
   switch (B) {
-    case 16: k_range_pack<16><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, gthr, apack, a32); break;
-    case 8: k_range_pack<8><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, gthr, apack, a32); break;
-    case 4: k_range_pack<4><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, gthr, apack, a32); break;
-    case 2: k_range_pack<2><<<grid, threads, 0, st>>>(imgs, rec, n_act, Kp, mom, gthr, apack, a32); break;
+    case 16: e = FIC_RP(16); break;
+    case 8: e = FIC_RP(8); break;
+    case 4: e = FIC_RP(4); break;
+    case 2: e = FIC_RP(2); break;
     default: return FIC_EINVAL;
   }
-  return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
+#undef FIC_RP
+  return e == cudaSuccess ? FIC_OK : FIC_ECUDA;
 }
 
 // ---------------------------------------------------------------- plan
@@ -127,6 +132,7 @@ __global__ void k_plan(int n_images, const int64_t* __restrict__ act_off,
                        int64_t* __restrict__ item_off, int32_t* __restrict__ chunks,
                        int32_t* __restrict__ acc_cnt, int32_t* __restrict__ rej_cnt,
                        int32_t* __restrict__ tile_acc, int n_tiles) {
+  grid_dep_sync();
   if (blockIdx.x != 0) return;
   if (tile_acc)
     for (int i = threadIdx.x; i < n_tiles; i += blockDim.x) tile_acc[i] = 0;
@@ -183,6 +189,7 @@ k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec
                int32_t* __restrict__ tile_acc, PosMoments pm) {
   constexpr int n = B * B;
   const int lane = threadIdx.x & 31;
+  grid_dep_sync();
   const int64_t N = *n_act;
   const bool overflow = meta->overflow != 0;
   if (overflow && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusOverflow);
@@ -327,20 +334,20 @@ int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const in
   const int64_t gmax = nsm > 0 ? 8 * (int64_t)nsm : 65535;
   const int grid = (int)std::min<int64_t>(ceil_div64(cap > 0 ? cap : 1, kReduceWarps), gmax);
   const double e_thr = (double)(B * B) * (rms * rms);
-#define FIC_RF(BB)                                                                            \
-  k_reduce_final<BB><<<grid, threads, 0, st>>>(imgs, rec, n_act, act_off, pool_off, n_images,  \
-                                               L, sel, item_off, chunks, part, iso_rows, S,   \
-                                               level, meta, status, res, e_thr, last, acc,    \
-                                               acc_cnt, rej_cnt, tile_acc, pm)
+  cudaError_t e;
+#define FIC_RF(BB)                                                                             \
+  launch_dep(k_reduce_final<BB>, dim3(grid), dim3(threads), 0, st, imgs, rec, n_act, act_off,   \
+             pool_off, n_images, L, sel, item_off, chunks, part, iso_rows, S, level, meta,       \
+             status, res, e_thr, last, acc, acc_cnt, rej_cnt, tile_acc, pm)
   switch (B) {
-    case 16: FIC_RF(16); break;
-    case 8: FIC_RF(8); break;
-    case 4: FIC_RF(4); break;
-    case 2: FIC_RF(2); break;
+    case 16: e = FIC_RF(16); break;
+    case 8: e = FIC_RF(8); break;
+    case 4: e = FIC_RF(4); break;
+    case 2: e = FIC_RF(2); break;
     default: return FIC_EINVAL;
   }
 #undef FIC_RF
-  return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
+  return e == cudaSuccess ? FIC_OK : FIC_ECUDA;
 }
 
 // ---------------------------------------------------------------- quadtree split
@@ -358,6 +365,7 @@ k_split_scan(int n_images, const int32_t* __restrict__ acc_cnt,
              const int32_t* __restrict__ rej_cnt, int64_t* __restrict__ code_off,
              int64_t* __restrict__ next_off, int64_t* __restrict__ next_cnt,
              int64_t* __restrict__ next_n, int32_t* tile_acc, int n_tiles, int64_t* total) {
+  grid_dep_sync();
   block_scan_counts(tile_acc, n_tiles, total);
   if (threadIdx.x != 0) return;
   int64_t a = 0, c = 0;
@@ -404,6 +412,7 @@ struct SplitCompact {
 __global__ void __launch_bounds__(kScanTile)
 k_split_scatter(SplitCompact f, const int32_t* __restrict__ tile_off) {
   __shared__ int sw[32];
+  grid_dep_sync();
   const int64_t n = f.size();
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   if (base >= n) return;  // uniform per block
@@ -420,11 +429,13 @@ int launch_split(const fic_transform* res, const RangeRec* rec, const int64_t* n
                  int64_t* next_off, int64_t* next_cnt, int64_t* next_n, int32_t* tile_acc,
                  int64_t* total, cudaStream_t st) {
   const int nb = (int)ceil_div64(cap > 0 ? cap : 1, kScanTile);
-  k_split_scan<<<1, 1024, 0, st>>>(n_images, acc_cnt, rej_cnt, code_off, next_off, next_cnt,
-                                   next_n, tile_acc, nb, total);
+  cudaError_t e = launch_dep(k_split_scan, dim3(1), dim3(1024), 0, st, n_images,
+                             (const int32_t*)acc_cnt, (const int32_t*)rej_cnt, code_off, next_off,
+                             next_cnt, next_n, tile_acc, nb, total);
+  if (e != cudaSuccess) return FIC_ECUDA;
   SplitCompact sc{n_act, acc, res, rec, codes, next, B / 2};
-  k_split_scatter<<<nb, kScanTile, 0, st>>>(sc, tile_acc);
-  return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
+  e = launch_dep(k_split_scatter, dim3(nb), dim3(kScanTile), 0, st, sc, (const int32_t*)tile_acc);
+  return e == cudaSuccess ? FIC_OK : FIC_ECUDA;
 }
 
 }  // namespace fic

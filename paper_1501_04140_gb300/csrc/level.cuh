@@ -53,6 +53,7 @@ struct MatchArgs {
   uint32_t* status;                 // device status word
   PosMoments pm;                    // the exact-s mode's V of a key
   int inject;                       // test hook (kInjectDropTileCopy), 0 normally
+  int groups_per_tile;              // tensor path, B <= 8: 1 or 2 epilogue groups per tile
 };
 
 // Test hook of the tensor matcher: the producer of CTA 0 leaves the first

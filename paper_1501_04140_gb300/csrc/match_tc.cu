@@ -98,7 +98,10 @@ struct TcWarps {
                 "register split exceeds the launch budget");
 };
 
-template <int B>
+// G: epilogue warp groups per tile at B <= 8 (2: a warp scores 8 of the
+// tile's 16 ranges per visit; 1: all 16, in two 64-column halves), a shape
+// the autotuner chooses per level; B = 16 always takes whole tiles.
+template <int B, int G = 2>
 struct TcCfg {
   static constexpr int EG = B == 16 ? 2 : 4;          // epilogue warp groups
   using Wp = TcWarps<EG>;
@@ -129,12 +132,14 @@ struct TcCfg {
   // B <= 8: two groups score each tile, a warp two of its four chunks; it
   // loads both, hands the accumulator back, then scores them.  B = 16: one
   // group per tile.
-  static constexpr int GPT = UNI ? 2 : 1;             // warp groups per tile
+  static constexpr int GPT = UNI ? G : 1;             // warp groups per tile
   static constexpr int TSETS = EG / GPT;              // tiles scored at once
-  // MMA issuers: at B <= 8 one per tile set (warps 1 and 2), so that the
-  // refill of one set's accumulators never waits behind the other set's
-  static constexpr int NMMA = UNI ? TSETS : 1;
+  // MMA issuers: at B <= 8 two (warps 1 and 2), each the tiles of every
+  // other tile set, so that the refill of one set's accumulators never
+  // waits behind the other set's
+  static constexpr int NMMA = UNI ? (TSETS < 2 ? TSETS : 2) : 1;
   static_assert(GPT == 1 || (NCH == 2 * GPT && NKC == 1), "two chunks per warp");
+  static_assert(!UNI || ((NCH / GPT) % 2 == 0 && (G == 1 || G == 2)), "64-column halves");
   static constexpr int MRG_BYTES = Wp::EPI_WARPS * kTileRanges * 16;  // per-warp range bests
   static constexpr int SCR_BYTES = 3 * kTileRanges * 4;  // per range: w, delta, threshold
   static constexpr int OFF_B = NA * A_BYTES;
@@ -223,11 +228,12 @@ __device__ inline float thr_exact(int64_t C, int64_t V) {
   return -__double2float_rd(gd * (1.0 - 0x1p-50));
 }
 
-template <int B, int MODE>
-__global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs a) {
-  using Cf = TcCfg<B>;
+template <int B, int MODE, int G>
+__global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchArgs a) {
+  using Cf = TcCfg<B, G>;
   constexpr int n = B * B;
   constexpr int LOGN = B == 16 ? 8 : B == 8 ? 6 : B == 4 ? 4 : 2;
+  grid_dep_sync();
   constexpr int CW = Cf::CW;
   extern __shared__ __align__(128) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -746,29 +752,31 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
         };
 
         if constexpr (Cf::UNI) {
-          // this warp's chunks two at a time (one 64-column load each),
-          // screened down to the smallest margin score - threshold of the
-          // lane's ranges; nothing else stays in registers.  In the rare case
-          // that some lane passes, the exact pass reads each range's 8
-          // correlations from tensor memory again and recomputes its maximum
-          // and score (the same arithmetic, so the same values) against the
-          // current threshold (never looser than a valid bound); then the
-          // accumulator goes back to the MMA.
+          // this warp's chunks (8 ranges per 64-column half, one or two
+          // halves), screened down to the smallest margin score - threshold
+          // of the lane's ranges; each range's margin stays in a register.
+          // In the rare case that some lane passes, the exact pass visits the
+          // ranges some lane flagged, reads each one's 8 correlations from
+          // tensor memory again and recomputes its maximum and score (the
+          // same arithmetic, so the same values) against the current
+          // threshold (never looser than a valid bound: a threshold only
+          // tightens, and a looser value left by a lost race is still a
+          // valid bound); after the last half the accumulator goes back to
+          // the MMA.
           constexpr int CPW = Cf::NCH / Cf::GPT;  // chunks per warp
-          constexpr int NRW = CPW * RPC;          // ranges per warp and tile
           const int c0 = CPW * cp;
-          float m = INFINITY;
-          // each range's margin stays in a register for the rare exact pass,
-          // which then visits only the ranges some lane of the warp flagged
-          float dm[NRW];
+          const DomRec* drp = sDom + dl;
+#pragma unroll 1
+          for (int h2 = 0; h2 < CPW; h2 += 2) {
+            const int cb = c0 + h2;  // first chunk of the half
+            const int rb0 = cb * RPC;
+            float m = INFINITY;
+            float dm[8];
 #pragma unroll
-          for (int j = 0; j < NRW; ++j) dm[j] = INFINITY;
-          if (ok) {
-#pragma unroll
-            for (int h2 = 0; h2 < CPW; h2 += 2) {
+            for (int j = 0; j < 8; ++j) dm[j] = INFINITY;
+            if (ok) {
               uint32_t ra[32], rb[32];
-              ptx::tmem_ld64_wait(tb + (c0 + h2) * 32, ra, rb);
-              const int rb0 = (c0 + h2) * RPC;  // first range of the pair of chunks
+              ptx::tmem_ld64_wait(tb + cb * 32, ra, rb);
               const float4 wa = *(const float4*)(sW + rb0), wb = *(const float4*)(sW + rb0 + 4);
               const float4 ta = *(const float4*)(sThr + rb0), tq = *(const float4*)(sThr + rb0 + 4);
               const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
@@ -784,14 +792,14 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
                   const float sa = score(cm[j], wv[j]), sb = score(cm[j + 1], wv[j + 1]);
-                  dm[h2 * RPC + j] = sa - tv[j];
-                  dm[h2 * RPC + j + 1] = sb - tv[j + 1];
-                  m = ptx::fmin3(m, dm[h2 * RPC + j], dm[h2 * RPC + j + 1]);
+                  dm[j] = sa - tv[j];
+                  dm[j + 1] = sb - tv[j + 1];
+                  m = ptx::fmin3(m, dm[j], dm[j + 1]);
                 }
               } else {
-                // two ranges per packed FMA: y = cmax - w sum Ds', the
-                // scores F_t - p_t y and the margins (a float difference is
-                // <= 0 exactly when sc <= thr)
+                // two ranges per packed FMA: y = cmax - w sum Ds', the scores
+                // F_t - p_t y and the margins (a float difference is <= 0
+                // exactly when sc <= thr)
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
                   const float2 y2 = __ffma2_rn(make_float2(nX, nX), make_float2(wv[j], wv[j + 1]),
@@ -802,46 +810,43 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
                     s2 = make_float2(fminf(s2.x, s1.x), fminf(s2.y, s1.y));
                   }
                   const float2 d2 = __fadd2_rn(s2, make_float2(-tv[j], -tv[j + 1]));
-                  dm[h2 * RPC + j] = d2.x;
-                  dm[h2 * RPC + j + 1] = d2.y;
+                  dm[j] = d2.x;
+                  dm[j + 1] = d2.y;
                   m = ptx::fmin3(m, d2.x, d2.y);
                 }
               }
             }
-          }
-          if (__any_sync(0xffffffffu, dvalid && m <= 0.f)) {
-            const DomRec dr = sDom[dl];
-            // the ranges that some lane's screen passed (a range no lane
-            // passed cannot pass now: thresholds only tighten, and a looser
-            // value left by a lost race is still a valid bound)
-            uint32_t fl = 0;
+            if (__any_sync(0xffffffffu, dvalid && m <= 0.f)) {
+              const DomRec dr = *drp;
+              uint32_t fl = 0;
 #pragma unroll
-            for (int j = 0; j < NRW; ++j) fl |= (dvalid && dm[j] <= 0.f) ? 1u << j : 0u;
-            uint32_t wm = __reduce_or_sync(0xffffffffu, fl);
+              for (int j = 0; j < 8; ++j) fl |= (dvalid && dm[j] <= 0.f) ? 1u << j : 0u;
+              uint32_t wm = __reduce_or_sync(0xffffffffu, fl);
 #pragma unroll 1
-            for (; wm; wm &= wm - 1) {
-              const int j = __ffs(wm) - 1;
-              const int r = c0 * RPC + j;
-              float v[8];
-              ptx::tmem_ld8_wait(tb + c0 * 32 + 8 * j, v);
-              const float cmj = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
-                                      ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
-              const float scj = score(cmj, sW[r]);
-              const bool mine = dvalid && scj <= sThr[r];
-              if (!__any_sync(0xffffffffu, mine)) continue;
-              bool need = mine;  // exact s: every flagged lane (no shared margin)
-              if constexpr (MODE != MODE_EXACT) {
-                float mn = mine ? scj : INFINITY;
+              for (; wm; wm &= wm - 1) {
+                const int j = __ffs(wm) - 1;
+                const int r = rb0 + j;
+                float v[8];
+                ptx::tmem_ld8_wait(tb + cb * 32 + 8 * j, v);
+                const float cmj = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
+                                        ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
+                const float scj = score(cmj, sW[r]);
+                const bool mine = dvalid && scj <= sThr[r];
+                if (!__any_sync(0xffffffffu, mine)) continue;
+                bool need = mine;  // exact s: every flagged lane (no shared margin)
+                if constexpr (MODE != MODE_EXACT) {
+                  float mn = mine ? scj : INFINITY;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-                const float lim = __fadd_ru(mn, 2.0f * sDelta[r]);
-                need = mine && scj <= lim;
+                  for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                  const float lim = __fadd_ru(mn, 2.0f * sDelta[r]);
+                  need = mine && scj <= lim;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, need);
+                int64_t be = INT64_MAX, bv = 0, bk = INT64_MAX;
+                if (need) pair_exact(v, cmj, sW[r], dr, be, bv, bk);
+                warp_best(be, bv, bk, bal);
+                resolve(r, be, bv, bk);
               }
-              const unsigned bal = __ballot_sync(0xffffffffu, need);
-              int64_t be = INT64_MAX, bv = 0, bk = INT64_MAX;
-              if (need) pair_exact(v, cmj, sW[r], dr, be, bv, bk);
-              warp_best(be, bv, bk, bal);
-              resolve(r, be, bv, bk);
             }
           }
           ptx::tc_fence_before();
@@ -903,49 +908,57 @@ __global__ void __launch_bounds__(TcCfg<B>::Wp::THREADS, 1) k_match_tc(MatchArgs
 }
 
 // ---------------------------------------------------------------- host side
-template <int B, int MODE>
-static int launch_tc_BM(const MatchArgs& a, int grid, cudaStream_t st) {
-  k_match_tc<B, MODE><<<grid, TcCfg<B>::Wp::THREADS, TcCfg<B>::SMEM + 128, st>>>(a);
-  return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
+template <int B, int MODE, int G>
+static int launch_tc_BMG(const MatchArgs& a, int grid, cudaStream_t st) {
+  using Cf = TcCfg<B, G>;
+  return launch_dep(k_match_tc<B, MODE, G>, dim3(grid), dim3(Cf::Wp::THREADS), Cf::SMEM + 128, st,
+                    a) == cudaSuccess
+             ? FIC_OK
+             : FIC_ECUDA;
 }
 
-template <int B, int MODE>
-static int prepare_BM() {
-  if (cudaFuncSetAttribute(k_match_tc<B, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           TcCfg<B>::SMEM + 128) != cudaSuccess)
+template <int B, int MODE, int G>
+static int prepare_BMG() {
+  using Cf = TcCfg<B, G>;
+  if (cudaFuncSetAttribute(k_match_tc<B, MODE, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           Cf::SMEM + 128) != cudaSuccess)
     return 1;
   // the warpgroups' register split is paid for by the launch allocation
   cudaFuncAttributes at{};
-  if (cudaFuncGetAttributes(&at, k_match_tc<B, MODE>) != cudaSuccess) return 1;
-  return at.numRegs >= TcCfg<B>::Wp::LREGS ? 0 : 1;
+  if (cudaFuncGetAttributes(&at, k_match_tc<B, MODE, G>) != cudaSuccess) return 1;
+  return at.numRegs >= Cf::Wp::LREGS ? 0 : 1;
 }
 
-template <int B>
-static int prepare_B() {
-  return prepare_BM<B, MODE_M1>() | prepare_BM<B, MODE_M2>() | prepare_BM<B, MODE_GRID>() |
-         prepare_BM<B, MODE_EXACT>();
+template <int B, int G>
+static int prepare_BG() {
+  return prepare_BMG<B, MODE_M1, G>() | prepare_BMG<B, MODE_M2, G>() |
+         prepare_BMG<B, MODE_GRID, G>() | prepare_BMG<B, MODE_EXACT, G>();
 }
 
 // Opt the matcher kernels in to their shared memory (once per device, before
 // any launch or stream capture).
 int match_tc_prepare() {
-  return (prepare_B<16>() | prepare_B<8>() | prepare_B<4>() | prepare_B<2>()) ? FIC_ECUDA : FIC_OK;
+  return (prepare_BG<16, 1>() | prepare_BG<8, 2>() | prepare_BG<8, 1>() | prepare_BG<4, 2>() |
+          prepare_BG<4, 1>() | prepare_BG<2, 2>() | prepare_BG<2, 1>())
+             ? FIC_ECUDA
+             : FIC_OK;
 }
 
-template <int B>
-static int launch_tc_B(const MatchArgs& a, int grid, cudaStream_t st) {
-  if (a.S.exact) return launch_tc_BM<B, MODE_EXACT>(a, grid, st);
-  if (a.S.grid) return launch_tc_BM<B, MODE_GRID>(a, grid, st);
-  if (a.S.m > 1) return launch_tc_BM<B, MODE_M2>(a, grid, st);
-  return launch_tc_BM<B, MODE_M1>(a, grid, st);
+template <int B, int G>
+static int launch_tc_BG(const MatchArgs& a, int grid, cudaStream_t st) {
+  if (a.S.exact) return launch_tc_BMG<B, MODE_EXACT, G>(a, grid, st);
+  if (a.S.grid) return launch_tc_BMG<B, MODE_GRID, G>(a, grid, st);
+  if (a.S.m > 1) return launch_tc_BMG<B, MODE_M2, G>(a, grid, st);
+  return launch_tc_BMG<B, MODE_M1, G>(a, grid, st);
 }
 
 int launch_match_tc(const MatchArgs& a, int grid, cudaStream_t st) {
+  const bool g1 = a.groups_per_tile == 1;
   switch (a.B) {
-    case 16: return launch_tc_B<16>(a, grid, st);
-    case 8: return launch_tc_B<8>(a, grid, st);
-    case 4: return launch_tc_B<4>(a, grid, st);
-    case 2: return launch_tc_B<2>(a, grid, st);
+    case 16: return launch_tc_BG<16, 1>(a, grid, st);
+    case 8: return g1 ? launch_tc_BG<8, 1>(a, grid, st) : launch_tc_BG<8, 2>(a, grid, st);
+    case 4: return g1 ? launch_tc_BG<4, 1>(a, grid, st) : launch_tc_BG<4, 2>(a, grid, st);
+    case 2: return g1 ? launch_tc_BG<2, 1>(a, grid, st) : launch_tc_BG<2, 2>(a, grid, st);
     default: return FIC_EINVAL;
   }
 }

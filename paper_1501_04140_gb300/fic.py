@@ -115,6 +115,8 @@ _SIGS = {
     "fic_code_set_profiling": (C.c_int, [_P, C.c_int]),
     "fic_code_profile": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
     "fic_code_graph_kernels": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "fic_code_pool_profile": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
+    "fic_code_schedule": (C.c_int, [_P, C.POINTER(C.c_int32), C.c_int]),
     "fic_decode": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_double, _P, C.c_int, C.c_int, _P,
                              C.POINTER(C.c_int)]),
     "fic_decode_static": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_double, _P,
@@ -368,13 +370,21 @@ class Code:
         _check(load().fic_code_count(self._h, image_idx, C.byref(c)), "fic_code_count")
         return c.value
 
-    def transforms(self, image_idx: int = 0) -> np.ndarray:
+    def transforms(self, image_idx: int = 0, out=None) -> np.ndarray:
+        """The saved maps of one image (fic_code_get).  With `out` (a 1-D
+        TRANSFORM_DTYPE array, e.g. a view of page-locked memory, large enough
+        for every map) the maps are copied into it and out[:count] is
+        returned; otherwise a new array."""
         n = self.count(image_idx)
-        out = np.zeros(max(n, 1), TRANSFORM_DTYPE)
+        fresh = out is None
+        if fresh:
+            out = np.zeros(max(n, 1), TRANSFORM_DTYPE)
+        elif out.dtype != TRANSFORM_DTYPE or out.ndim != 1 or not out.flags.c_contiguous:
+            raise TypeError("out must be a contiguous 1-D TRANSFORM_DTYPE array")
         c = C.c_size_t()
         _check(load().fic_code_get(self._h, image_idx, out.ctypes.data, len(out), C.byref(c)),
                "fic_code_get")
-        return out[:c.value].copy()
+        return out[:c.value].copy() if fresh else out[:c.value]
 
     def stats(self, image_idx: int = 0) -> list[dict]:
         arr = (fic_level_stats * 4)()
@@ -414,6 +424,20 @@ class Code:
         nl = 1 if self.params.single_level else self.params.n_levels
         arr = (C.c_float * (2 * nl))()
         _check(load().fic_code_profile(self._h, arr, 2 * nl), "fic_code_profile")
+        return [(arr[2 * i], arr[2 * i + 1]) for i in range(nl)]
+
+    def pool_profile(self) -> list[float]:
+        """Per level: ms of the pool build of the last encode (profiling on)."""
+        nl = 1 if self.params.single_level else self.params.n_levels
+        arr = (C.c_float * nl)()
+        _check(load().fic_code_pool_profile(self._h, arr, nl), "fic_code_pool_profile")
+        return [arr[i] for i in range(nl)]
+
+    def schedule(self) -> list[tuple[int, int]]:
+        """Per level: (work items per CTA, epilogue groups per tile) of the matcher."""
+        nl = 1 if self.params.single_level else self.params.n_levels
+        arr = (C.c_int32 * (2 * nl))()
+        _check(load().fic_code_schedule(self._h, arr, 2 * nl), "fic_code_schedule")
         return [(arr[2 * i], arr[2 * i + 1]) for i in range(nl)]
 
     def graph_kernels(self) -> int:
