@@ -180,6 +180,82 @@ def _job_rate(ws: int, units_per_rank: float, seconds: float) -> float:
     return ws * units_per_rank / seconds
 
 
+# Algorithmic bytes of the HBM-bound steps of one level (summed over the
+# images), from the level's counts:
+# - pool build (Sec. 3): the images read once; per pool position its entropy
+#   key and its two moments written (16 B); per kept domain its index (4 B),
+#   its operand row (2 K_p B, f16) and its scoring records (32 B);
+# - the rest of the level chain: per active range its pixels (n B) and its
+#   domain's (4n B) read, its 8 operand rows written (16 K_p B), and about
+#   300 B of moments, candidates, the map and the split's records.
+def _kp(B):
+    return max(16, B * B)
+
+
+def pool_bytes(B, s, px_total):
+    return float(px_total + 16 * s["pool_size_total"] + s["n_kept"] * (4 + 2 * _kp(B) + 32))
+
+
+def chain_bytes(B, s):
+    return float(s["n_active"] * (5 * B * B + 16 * _kp(B) + 300))
+
+
+def oracle_extrapolated(img, stats, n_ranges, smode):
+    """The oracle on the first n_ranges level-1 ranges of the 4096 x 4096
+    workload (the whole level-1 kept pool, a bounded slice of it per call),
+    timed and extrapolated linearly to every match of the encode: labelled
+    "extrapolated"."""
+    import oracle
+    cores = os.cpu_count() or 1
+    B = stats[0]["size"]
+    _, kept, _, _ = oracle.pool_filter(img, B, 1, 0.5)
+    sp, q = oracle.s_set(1 if smode else 0, smode.get("grid_samples", 16), B)
+    H, W = img.shape
+    xy = np.array([(x, y) for y in range(0, H, B) for x in range(0, W, B)][:n_ranges], np.int32)
+    t0 = time.perf_counter()
+    for c0 in range(0, len(kept), 1 << 19):
+        oracle.match(img, B, 1, kept[c0:c0 + (1 << 19)], xy, sp, q, n_threads=cores)
+    dt = time.perf_counter() - t0
+    rate = len(xy) * len(kept) * 8 / dt
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "extrapolated": True,
+            "sample": f"first {len(xy)} level-1 ranges x {len(kept)} kept domains x 8 in "
+                      f"{dt:.1f}s, extrapolated to the encode's matches at that rate",
+            "encode_s_extrapolated": sum(s["matches"] for s in stats) / rate,
+            "cpu_model": _cpu_model()}
+
+
+def measure_batch64(ctx, stream, l2_flush, steps=3, warmup=3):
+    """Encode time of the 64-image uneven batch (graph replay, CUDA events,
+    L2 flushed between steps): matches/s and ms per batch and per image."""
+    import torch
+    from paper_1501_04140_gb300 import fic
+    imgs = workload_images("batch64")
+    d = [torch.from_numpy(im).cuda() for im in imgs]
+    p = fic.default_params()
+    code = ctx.encode(d, p, stream=stream)
+    torch.cuda.synchronize()
+    matches = sum(sum(s["matches"] for s in code.stats(i)) for i in range(len(imgs)))
+    for _ in range(warmup):
+        ctx.encode_again(code, d, p, stream=stream)
+    times = []
+    for _ in range(steps):
+        l2_flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.encode_again(code, d, p, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    code.free()
+    ms = statistics.mean(times)
+    return {"workload": WORKLOADS["batch64"]["desc"], "value": matches / (ms * 1e-3),
+            "unit": UNIT, "ms_per_batch": ms, "ms_per_image": ms / len(imgs),
+            "n_images": len(imgs), "matches_per_batch": matches, "steps": steps,
+            "warmup": warmup}
+
+
 # ------------------------------------------------------------------ oracle
 def oracle_rate(img, level_stats, budget_s: float, n_threads: int):
     """The oracle's matches/s on a bounded sample: per level, the exhaustive
@@ -454,9 +530,12 @@ def run_ours(args):
     d_img = d_imgs if len(d_imgs) > 1 else d_imgs[0]
     l2_flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
+    smode = dict(s_mode=fic.FIC_S_GRID, grid_samples=int(args.smode[4:])) \
+        if args.smode.startswith("grid") else {}
+
     def time_path(precision, steps, warmup, profile=False):
         p = fic.default_params(precision=precision, domain_step=wl["step"],
-                               autotune=1 if args.autotune else 0)
+                               autotune=1 if args.autotune else 0, **smode)
         with torch.cuda.stream(stream):
             code = ctx.encode(d_img, p, stream=stream)
         torch.cuda.synchronize()
@@ -467,6 +546,7 @@ def run_ours(args):
             agg = dict(per_img[0][lv])
             for k in ("n_active", "n_kept", "matches"):
                 agg[k] = sum(ps[lv][k] for ps in per_img)
+            agg["pool_size_total"] = sum(ps[lv]["pool_size"] for ps in per_img)
             stats.append(agg)
         if profile:
             code.set_profiling(True)
@@ -489,7 +569,8 @@ def run_ours(args):
                 times.append(e0.elapsed_time(e1))
                 if profile and prof is not None:
                     try:
-                        prof.append(code.profile())
+                        prof.append([lv + (pm,) for lv, pm in zip(code.profile(),
+                                                                  code.pool_profile())])
                     except fic.FicError as e:  # events inside the graph unusable
                         print(f"in-graph profile failed ({e}); timing kernels outside it",
                               file=sys.stderr)
@@ -501,7 +582,7 @@ def run_ours(args):
             for _ in range(max(3, steps // 2)):
                 l2_flush.zero_()
                 ctx.encode_again(code, d_img, p, stream=None)
-                prof.append(code.profile())
+                prof.append([lv + (pm,) for lv, pm in zip(code.profile(), code.pool_profile())])
         return code, stats, times, prof, clk.summary()
 
     # exact tensor path (timed, with per-level matcher events inside the graph)
@@ -510,6 +591,7 @@ def run_ours(args):
     matches = sum(s["matches"] for s in stats)
     ms = statistics.mean(times)
     n_kernels = code.graph_kernels()
+    sched = code.schedule()
     dec = code.decode(0)
     psnr = oracle.psnr(img, dec)  # the first image
 
@@ -529,24 +611,42 @@ def run_ours(args):
     alu_peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e12  # Top/s
     lv_ms = [statistics.mean(p[l][0] for p in prof) for l in range(len(stats))]
     lv_all = [statistics.mean(p[l][1] for p in prof) for l in range(len(stats))]
+    lv_pool = [statistics.mean(p[l][2] for p in prof) for l in range(len(stats))]
+    px_total = sum(im.size for im in imgs)
     levels = []
     for l, s in enumerate(stats):
         B = s["size"]
-        n_s = 1 if B == 16 else 2  # predefined S of Sec. 3.1
+        # |S|: the predefined sets of Sec. 3.1, or the grid (whose epilogue
+        # scores the 3 grid points around the real minimiser)
+        n_s = (1 if B == 16 else 2) if not smode else 3
         flop = 2.0 * B * B * s["matches"]
         ops = (8 + 2 * n_s) / 8.0 * s["matches"]
         sec = lv_ms[l] * 1e-3
         tensor_bound = flop / (bf16 * 1e12) >= ops / (alu_peak * 1e12)
         ach = (flop if tensor_bound else ops) / sec / 1e12 if sec > 0 else 0.0
         pk = bf16 if tensor_bound else alu_peak
+        pool_b, other_b = pool_bytes(B, s, px_total), chain_bytes(B, s)
+        other_ms = lv_all[l] - lv_ms[l]
         levels.append({"B": B, "n_active": s["n_active"], "n_kept": s["n_kept"],
                        "matches": s["matches"], "matcher_ms": lv_ms[l], "level_ms": lv_all[l],
+                       "schedule": {"items_per_cta": sched[l][0],
+                                    "groups_per_tile": sched[l][1]},
+                       # the level's pool build (side stream) and the rest of its
+                       # chain (range operand, plan, reduction, split): HBM-bound
+                       # in design; algorithmic bytes over the measured time
+                       "pool_ms": lv_pool[l], "pool_bytes": pool_b,
+                       "pool_hbm_frac": pool_b / (lv_pool[l] * 1e-3) / (hbm * 1e9)
+                       if lv_pool[l] > 0 else 0.0,
+                       "chain_ms": other_ms, "chain_bytes": other_b,
+                       "chain_hbm_frac": other_b / (other_ms * 1e-3) / (hbm * 1e9)
+                       if other_ms > 0 else 0.0,
                        "bound": "tensor" if tensor_bound else "alu",
                        "achieved": ach, "unit": "TFLOP/s" if tensor_bound else "Top/s",
                        "frac": ach / pk if pk else 0.0,
                        "matches_per_s": s["matches"] / sec if sec > 0 else 0.0,
                        # every (range, domain, isometry, s) of the level's set
-                       "s_evaluations_per_s": n_s * s["matches"] / sec if sec > 0 else 0.0})
+                       "s_evaluations_per_s": (smode.get("grid_samples", n_s)) * s["matches"] / sec
+                       if sec > 0 else 0.0})
     dom = max(range(len(levels)), key=lambda l: levels[l]["matcher_ms"])
     d = levels[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"],
@@ -561,24 +661,45 @@ def run_ours(args):
     # plain FP32 CUDA-core path, same workload (not on the 4096 x 4096 run,
     # where one FP32 encode takes minutes)
     fp32 = None
-    if args.workload != "4096":
-        code32, stats32, times32, _, _ = time_path(fic.FIC_PREC_FP32, max(3, args.steps // 4), 3)
+    if args.workload != "4096" or args.fp32_4096:
+        # (4096 x 4096: one FP32 encode takes tens of seconds, so one warm-up
+        # and one timed encode, stated in the line)
+        big = args.workload == "4096"
+        fp_steps, fp_warm = (1, 1) if big else (max(3, args.steps // 4), 3)
+        code32, stats32, times32, prof32, _ = time_path(fic.FIC_PREC_FP32, fp_steps, fp_warm,
+                                                        profile=True)
         ms32 = statistics.mean(times32)
         psnr32 = oracle.psnr(img, code32.decode(0))
         matches32 = sum(s["matches"] for s in stats32)
         code32.free()
+        # the FP32 matcher per level: 2n FMA flops per match (its SGEMM of the
+        # isometry rows against the domains) against the FP32 FMA roof
+        fma_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+        lv32 = []
+        for l, s32 in enumerate(stats32):
+            B = s32["size"]
+            m_ms = statistics.mean(p[l][0] for p in prof32)
+            tf = 2.0 * B * B * s32["matches"] / (m_ms * 1e-3) / 1e12 if m_ms > 0 else 0.0
+            lv32.append({"B": B, "matches": s32["matches"], "matcher_ms": m_ms,
+                         "level_ms": statistics.mean(p[l][1] for p in prof32),
+                         "achieved": tf, "unit": "TFLOP/s", "peak": fma_peak, "frac": tf / fma_peak,
+                         "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 x 2 x "
+                                        f"{sm_mhz:.0f} MHz (derived)"})
         fp32 = {"value": matches32 / (ms32 * 1e-3), "unit": UNIT, "encode_ms": ms32,
-                "psnr_db": psnr32,
+                "psnr_db": psnr32, "levels": lv32, "steps": fp_steps, "warmup": fp_warm,
                 "speedup_tensor_vs_fp32": (matches / (t_max * 1e-3)) / (matches32 / (ms32 * 1e-3))}
 
     # end to end through the C ABI with host buffers: pinned host images in,
     # every saved map out, both copies inside the timed region
     pinned = [torch.from_numpy(im).pin_memory() for im in imgs]
     ph = pinned if len(pinned) > 1 else pinned[0]
-    p = fic.default_params(domain_step=wl["step"])
+    p = fic.default_params(domain_step=wl["step"], **smode)
     code_h = ctx.encode(ph, p, stream=stream)
     torch.cuda.synchronize()
     n_codes = sum(code_h.count(i) for i in range(len(imgs)))
+    # page-locked output buffers, allocated once (room for every 2 x 2 range)
+    outs_buf = [torch.empty((im.size // 4) * fic.TRANSFORM_DTYPE.itemsize, dtype=torch.uint8,
+                            pin_memory=True).numpy().view(fic.TRANSFORM_DTYPE) for im in imgs]
     e2e = []
     e2e_steps = args.steps if args.workload == "512" else 1
     e2e_warm = args.warmup if args.workload == "512" else 1
@@ -586,20 +707,35 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.encode_again(code_h, ph, p, stream=stream)
-        outs = [code_h.transforms(i) for i in range(len(imgs))]
+        outs = [code_h.transforms(i, out=outs_buf[i]) for i in range(len(imgs))]
         t1 = time.perf_counter()
         if s >= e2e_warm:
             e2e.append(t1 - t0)
     e2e_v = _job_rate(ws, matches, _max_over_ranks(statistics.mean(e2e), ws, "cuda"))
-    d2h = sum(len(o) * o.dtype.itemsize for o in outs) + 4 * 8 * 2 * len(imgs)
+    # the maps, plus the one read-back of every level's code offsets and the
+    # status word
+    d2h = (sum(len(o) * o.dtype.itemsize for o in outs)
+           + 8 * 4 * (len(imgs) + 1) + 16)
     code_h.free()
+
+    # the 64-image uneven batch, a few graph replays (the same encoder, one
+    # launch per step and level over all images)
+    batch = None
+    if args.workload == "512" and not args.no_batch:
+        batch = measure_batch64(ctx, stream, l2_flush, steps=3, warmup=3)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "512":
         cores = os.cpu_count() or 1
         v, sample = oracle_rate(img, stats, args.cpu_budget, cores)
+        # and single-threaded, the way the paper ran its encoder (Sec. 4)
+        v1, sample1 = oracle_rate(img, stats, args.cpu_budget / 2, 1)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-               "cpu_model": _cpu_model()}
+               "cpu_model": _cpu_model(),
+               "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": sample1}}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "4096":
+        cpu = oracle_extrapolated(img, stats, args.oracle_ranges, smode)
 
     if rank == 0:
         line = {
@@ -607,11 +743,14 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16 MMA on exact integers, int64 scoring",
             "data": "synthetic",
-            "config": {"workload": wl["desc"], "parallelism": f"replicas x{ws}",
+            "config": {"workload": wl["desc"] if not smode else
+                       wl["desc"].replace("predefined S", f"{smode['grid_samples']}-sample s grid"),
+                       "parallelism": f"replicas x{ws}",
                        "l2": "flushed between steps (256 MB write)",
                        "encode_ms": t_max, "psnr_db": psnr, "n_codes": n_codes,
                        "n_images": len(imgs), "matches_per_step": matches},
             "fp32_path": fp32,
+            "batch64": batch,
             "levels": levels,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -639,6 +778,14 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=16.0,
                     help="seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--smode", default="predefined",
+                    help="predefined (Sec. 3.1's sets, the default) or gridM (an M-sample grid)")
+    ap.add_argument("--fp32-4096", action="store_true",
+                    help="also time the FP32 path on the 4096 x 4096 workload (minutes)")
+    ap.add_argument("--oracle-ranges", type=int, default=16,
+                    help="4096 workload: level-1 ranges the oracle is timed on (extrapolated)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the short 64-image batch measurement of the default run")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the library's default schedule (by default the library times "
                          "its schedules on the first encode and keeps the fastest)")

@@ -77,3 +77,16 @@ def test_gpu_identity_by_uuid(monkeypatch):
 
     monkeypatch.setattr(torch.cuda, "get_device_properties", boom)
     assert bench.gpu_identity(3) == "3"
+
+
+def test_algorithmic_bytes_of_the_hbm_bound_steps():
+    """The bytes behind the pool and chain HBM fractions, worked out by hand
+    for one level: B = 4 (K_p = 16), 1000 pool positions, 400 kept domains,
+    300 active ranges, 65536 image pixels."""
+    s = {"pool_size_total": 1000, "n_kept": 400, "n_active": 300}
+    # image once + 16 B per position + (4 + 2*16 + 32) B per kept domain
+    assert bench.pool_bytes(4, s, 65536) == 65536 + 16 * 1000 + 400 * (4 + 32 + 32)
+    # per active range: 5n pixels read + 16 K_p operand bytes + 300 B records
+    assert bench.chain_bytes(4, s) == 300 * (5 * 16 + 16 * 16 + 300)
+    # K_p is the MMA's K step at B = 2 (n = 4 padded to 16)
+    assert bench.pool_bytes(2, s, 0) == 16 * 1000 + 400 * (4 + 32 + 32)
