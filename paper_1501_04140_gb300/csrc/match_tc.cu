@@ -142,11 +142,18 @@ struct TcCfg {
   static_assert(!UNI || ((NCH / GPT) % 2 == 0 && (G == 1 || G == 2)), "64-column halves");
   static constexpr int MRG_BYTES = Wp::EPI_WARPS * kTileRanges * 16;  // per-warp range bests
   static constexpr int SCR_BYTES = 3 * kTileRanges * 4;  // per range: w, delta, threshold
+  // B <= 4 (the explicit and grid S sets): the exact pass is deferred to a
+  // per-warp queue of candidates (see the epilogue); B = 8 and the exact-s
+  // mode score candidates in place
+  static constexpr bool DEFER = B <= 4;
+  static constexpr int QCAP = DEFER ? 64 : 0;
+  static constexpr int Q_BYTES = Wp::EPI_WARPS * QCAP * 16;
   static constexpr int OFF_B = NA * A_BYTES;
   static constexpr int OFF_D = OFF_B + NST * ST_BYTES;
   static constexpr int OFF_MRG = OFF_D + ND * D_BYTES;
   static constexpr int OFF_SCR = OFF_MRG + MRG_BYTES;
-  static constexpr int OFF_BAR = OFF_SCR + SCR_BYTES;
+  static constexpr int OFF_Q = OFF_SCR + SCR_BYTES;
+  static constexpr int OFF_BAR = OFF_Q + Q_BYTES;
   static constexpr int NBAR = 2 * NST + 2 * NA + 2 * NACC + 2 * ND + 1;
   static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
   static constexpr int BYTES = OFF_MISC + 16;
@@ -157,6 +164,60 @@ struct TcCfg {
 };
 
 constexpr int MODE_M1 = 0, MODE_M2 = 1, MODE_GRID = 2, MODE_EXACT = 3;
+
+// A candidate pair queued for exact scoring (B <= 8): the domain's slot in
+// the level's kept pool, the pair's largest isometry correlation (an exact
+// integer) and the range in the item (grid S: and the nearest grid point of
+// the pair's float minimiser).
+struct QCand {
+  int64_t slot;  // kept-pool slot of the domain
+  int32_t cmax;  // largest isometry correlation of the pair
+  int32_t rk;    // range in the item (bits 0-7) | grid point << 12
+};
+static_assert(sizeof(QCand) == 16, "queue entry");
+
+// The 8 isometry correlations of a (domain, range) pair, recomputed by one
+// thread from the operands in global memory: the domain's row Ds - 512 in its
+// 128-domain tile block and the range's 8 rows T_k^-1 R - 128, both f16 in
+// the MMA's core-matrix layouts.  Every product and partial sum is an
+// integer below 2^22 (n <= 64), so the float sums are exact: the values the
+// MMA accumulated.
+template <int B, int KP, int TILE_BYTES>
+__device__ inline void pair_corr_global(const uint16_t* __restrict__ bpack,
+                                        const uint16_t* __restrict__ apack, int64_t slot,
+                                        int64_t range, float (&v)[8]) {
+  constexpr int n = B * B;
+  const uint16_t* dt =
+      (const uint16_t*)((const uint8_t*)bpack + (slot >> 7) * (int64_t)TILE_BYTES);
+  const int d = (int)(slot & 127);
+  const uint16_t* drow = dt + (d >> 3) * (KP / 8) * 64 + (d & 7) * 8;
+  const uint16_t* rrow = apack + range * 8 * KP;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = 0.f;
+#pragma unroll 1
+  for (int c = 0; c < (n + 7) / 8; ++c) {
+    const uint4 dq = __ldg((const uint4*)(drow + c * 64));
+    const uint32_t dw[4] = {dq.x, dq.y, dq.z, dq.w};
+    float df[8];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const float2 f = __half22float2(*(const __half2*)&dw[h]);
+      df[2 * h] = f.x;
+      df[2 * h + 1] = f.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint4 rq = __ldg((const uint4*)(rrow + (c * 8 + k) * 8));
+      const uint32_t rw[4] = {rq.x, rq.y, rq.z, rq.w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const float2 f = __half22float2(*(const __half2*)&rw[h]);
+        v[k] = fmaf(df[2 * h], f.x, v[k]);
+        v[k] = fmaf(df[2 * h + 1], f.y, v[k]);
+      }
+    }
+  }
+}
 
 struct ItemGeo {
   int im, nr, t0, t1, nkept;
@@ -444,6 +505,7 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
     const uint32_t epi_threads = 32 * Cf::Wp::EPI_WARPS;
     Cand* wbest = (Cand*)(smem + Cf::OFF_MRG);  // [EPI_WARPS][16]
     Cand* mybest = wbest + ew * kTileRanges;
+    QCand* myq = (QCand*)(smem + Cf::OFF_Q) + ew * Cf::QCAP;  // B <= 8
     float* sW = (float*)(smem + Cf::OFF_SCR);
     float* sDelta = sW + kTileRanges;
     float* sThr = sW + 2 * kTileRanges;
@@ -487,7 +549,83 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
       if (lane < kTileRanges) mybest[lane] = Cand{INT64_MAX, INT64_MAX};
       __syncwarp();
       uint32_t gpre = rv ? __ldcg(a.gthr + g.r0 + rl) : kThrInit;
+      int qn = 0;  // candidates in this warp's queue (warp-uniform)
       int nmine = 0;
+
+      // Exact scoring of the queued candidates (warp-collective): a lane per
+      // candidate computes its best exact E' and tie-break key over S (the
+      // arithmetic of pair_exact), then per range the warp's best merges
+      // into this warp's best of the range and tightens the range's
+      // threshold (as an exact pass does).
+      auto flush = [&]() {
+        if constexpr (Cf::DEFER && MODE != MODE_EXACT) {
+          const int m_s2 = a.S.m, qv2 = a.S.q;
+          for (int b0 = 0; b0 < qn; b0 += 32) {
+            const bool have = b0 + lane < qn;
+            int64_t be = INT64_MAX, bk = INT64_MAX;
+            int r = 0;
+            if (have) {
+              const QCand c = myq[b0 + lane];
+              r = c.rk & 0xff;
+              // the isometry of the largest correlation (lowest k on ties),
+              // from the pair's correlations recomputed exactly
+              float cv[8];
+              pair_corr_global<B, Cf::Kp, Cf::ST_BYTES>(a.bpack, a.apack, c.slot, g.r0 + r, cv);
+              const float cmf = (float)c.cmax;
+              int kmax = 7;
+#pragma unroll
+              for (int k = 6; k >= 0; --k)
+                if (cv[k] == cmf) kmax = k;
+              const DomRec dr = a.dom[c.slot];
+              const int64_t srp_r = (int64_t)(int)(sW[r] * (float)n);
+              const int64_t C = ((int64_t)c.cmax << LOGN) - srp_r * (int64_t)dr.sdp;
+              auto cand = [&](int64_t p, int si) {
+                const int64_t e = p * p * dr.v - 8 * p * qv2 * C;
+                const int64_t key = ((int64_t)dr.pos * 8 + (p > 0 ? kmax : 0)) * m_s2 + si;
+                if (e < be || (e == be && key < bk)) {
+                  be = e;
+                  bk = key;
+                }
+              };
+              if constexpr (MODE == MODE_GRID) {
+                const int pi = c.rk >> 12;
+                for (int pp = max(pi - 1, 0); pp <= min(pi + 1, qv2); ++pp) cand(pp, pp);
+              } else {
+                cand(a.S.p[0], 0);
+                if constexpr (MODE == MODE_M2) cand(a.S.p[1], 1);
+              }
+            }
+            for (uint32_t rm = __reduce_or_sync(0xffffffffu, have ? 1u << r : 0u); rm;
+                 rm &= rm - 1) {
+              const int rr = __ffs(rm) - 1;
+              int64_t e2 = have && r == rr ? be : INT64_MAX, k2 = have && r == rr ? bk : INT64_MAX;
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) {
+                const int64_t eo = __shfl_xor_sync(0xffffffffu, e2, o);
+                const int64_t ko = __shfl_xor_sync(0xffffffffu, k2, o);
+                if (eo < e2 || (eo == e2 && ko < k2)) {
+                  e2 = eo;
+                  k2 = ko;
+                }
+              }
+              const Cand cur = mybest[rr];
+              if (e2 < cur.score || (e2 == cur.score && k2 < cur.key)) {
+                const float to = thr_of(e2, inv_up, inv_dn, sDelta[rr]);
+                __syncwarp();
+                if (lane == 0) {
+                  mybest[rr] = Cand{e2, k2};
+                  if (to < sThr[rr]) {
+                    sThr[rr] = to;
+                    atomicMin(a.gthr + g.r0 + rr, thr_to_ord(to));
+                  }
+                }
+                __syncwarp();
+              }
+            }
+          }
+          qn = 0;
+        }
+      };
 
       // this group's tiles of the item: ti = tile counter of the CTA
       const uint32_t tib = ti;
@@ -752,106 +890,190 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
         };
 
         if constexpr (Cf::UNI) {
-          // this warp's chunks (8 ranges per 64-column half, one or two
-          // halves), screened down to the smallest margin score - threshold
-          // of the lane's ranges; each range's margin stays in a register.
-          // In the rare case that some lane passes, the exact pass visits the
-          // ranges some lane flagged, reads each one's 8 correlations from
-          // tensor memory again and recomputes its maximum and score (the
-          // same arithmetic, so the same values) against the current
-          // threshold (never looser than a valid bound: a threshold only
-          // tightens, and a looser value left by a lost race is still a
-          // valid bound); after the last half the accumulator goes back to
-          // the MMA.
+          // this warp's chunks: 8 ranges per 64-column half, one or two
+          // halves.  The float screen reduces each range's 8 correlations to
+          // their maximum and keeps each range's margin (score - threshold)
+          // in a register.
           constexpr int CPW = Cf::NCH / Cf::GPT;  // chunks per warp
+          constexpr int NH = CPW / 2;             // 64-column halves
           const int c0 = CPW * cp;
           const DomRec* drp = sDom + dl;
-#pragma unroll 1
-          for (int h2 = 0; h2 < CPW; h2 += 2) {
-            const int cb = c0 + h2;  // first chunk of the half
-            const int rb0 = cb * RPC;
-            float m = INFINITY;
-            float dm[8];
+          // the float screen of one half from its 8 maxima: margins dm and
+          // their minimum m
+          auto screen8 = [&](const float (&cm)[8], int rb0, float (&dm)[8], float& m) {
+            const float4 wa = *(const float4*)(sW + rb0), wb = *(const float4*)(sW + rb0 + 4);
+            const float4 ta = *(const float4*)(sThr + rb0), tq = *(const float4*)(sThr + rb0 + 4);
+            const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+            const float tv[8] = {ta.x, ta.y, ta.z, ta.w, tq.x, tq.y, tq.z, tq.w};
+            if constexpr (MODE == MODE_GRID || MODE == MODE_EXACT) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) dm[j] = INFINITY;
-            if (ok) {
-              uint32_t ra[32], rb[32];
-              ptx::tmem_ld64_wait(tb + cb * 32, ra, rb);
-              const float4 wa = *(const float4*)(sW + rb0), wb = *(const float4*)(sW + rb0 + 4);
-              const float4 ta = *(const float4*)(sThr + rb0), tq = *(const float4*)(sThr + rb0 + 4);
-              const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-              const float tv[8] = {ta.x, ta.y, ta.z, ta.w, tq.x, tq.y, tq.z, tq.w};
-              float cm[8];
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const float* v = (const float*)(j < RPC ? ra + 8 * j : rb + 8 * (j - RPC));
-                cm[j] = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
-                              ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
+              for (int j = 0; j < 8; j += 2) {
+                const float sa = score(cm[j], wv[j]), sb = score(cm[j + 1], wv[j + 1]);
+                dm[j] = sa - tv[j];
+                dm[j + 1] = sb - tv[j + 1];
+                m = ptx::fmin3(m, dm[j], dm[j + 1]);
               }
-              if constexpr (MODE == MODE_GRID || MODE == MODE_EXACT) {
+            } else {
+              // two ranges per packed FMA: y = cmax - w sum Ds', the scores
+              // F_t - p_t y and the margins (a float difference is <= 0
+              // exactly when sc <= thr)
 #pragma unroll
-                for (int j = 0; j < 8; j += 2) {
-                  const float sa = score(cm[j], wv[j]), sb = score(cm[j + 1], wv[j + 1]);
-                  dm[j] = sa - tv[j];
-                  dm[j + 1] = sb - tv[j + 1];
-                  m = ptx::fmin3(m, dm[j], dm[j + 1]);
+              for (int j = 0; j < 8; j += 2) {
+                const float2 y2 = __ffma2_rn(make_float2(nX, nX), make_float2(wv[j], wv[j + 1]),
+                                             make_float2(cm[j], cm[j + 1]));
+                float2 s2 = __ffma2_rn(make_float2(-p0f, -p0f), y2, make_float2(F0, F0));
+                if constexpr (MODE == MODE_M2) {
+                  const float2 s1 = __ffma2_rn(make_float2(-p1f, -p1f), y2, make_float2(F1, F1));
+                  s2 = make_float2(fminf(s2.x, s1.x), fminf(s2.y, s1.y));
                 }
-              } else {
-                // two ranges per packed FMA: y = cmax - w sum Ds', the scores
-                // F_t - p_t y and the margins (a float difference is <= 0
-                // exactly when sc <= thr)
+                const float2 d2 = __fadd2_rn(s2, make_float2(-tv[j], -tv[j + 1]));
+                dm[j] = d2.x;
+                dm[j + 1] = d2.y;
+                m = ptx::fmin3(m, d2.x, d2.y);
+              }
+            }
+          };
+          auto max8 = [&](const uint32_t (&ra)[32], const uint32_t (&rb)[32], float (&cm)[8]) {
 #pragma unroll
-                for (int j = 0; j < 8; j += 2) {
-                  const float2 y2 = __ffma2_rn(make_float2(nX, nX), make_float2(wv[j], wv[j + 1]),
-                                               make_float2(cm[j], cm[j + 1]));
-                  float2 s2 = __ffma2_rn(make_float2(-p0f, -p0f), y2, make_float2(F0, F0));
-                  if constexpr (MODE == MODE_M2) {
-                    const float2 s1 = __ffma2_rn(make_float2(-p1f, -p1f), y2, make_float2(F1, F1));
-                    s2 = make_float2(fminf(s2.x, s1.x), fminf(s2.y, s1.y));
+            for (int j = 0; j < 8; ++j) {
+              const float* v = (const float*)(j < RPC ? ra + 8 * j : rb + 8 * (j - RPC));
+              cm[j] = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
+                            ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
+            }
+          };
+          if constexpr (MODE == MODE_EXACT || !Cf::DEFER) {
+            // exact s, and B = 8 (where recomputing a queued pair's 8
+            // correlations from the operands costs more than holding the
+            // accumulator): the exact pass reads the flagged ranges'
+            // correlations from tensor memory again, so the accumulator goes
+            // back after the last half
+#pragma unroll 1
+            for (int h2 = 0; h2 < CPW; h2 += 2) {
+              const int cb = c0 + h2;  // first chunk of the half
+              const int rb0 = cb * RPC;
+              float m = INFINITY;
+              float dm[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) dm[j] = INFINITY;
+              if (ok) {
+                uint32_t ra[32], rb[32];
+                ptx::tmem_ld64_wait(tb + cb * 32, ra, rb);
+                float cm[8];
+                max8(ra, rb, cm);
+                screen8(cm, rb0, dm, m);
+              }
+              if (__any_sync(0xffffffffu, dvalid && m <= 0.f)) {
+                const DomRec dr = *drp;
+                uint32_t fl = 0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) fl |= (dvalid && dm[j] <= 0.f) ? 1u << j : 0u;
+                uint32_t wm = __reduce_or_sync(0xffffffffu, fl);
+#pragma unroll 1
+                for (; wm; wm &= wm - 1) {
+                  const int j = __ffs(wm) - 1;
+                  const int r = rb0 + j;
+                  float v[8];
+                  ptx::tmem_ld8_wait(tb + cb * 32 + 8 * j, v);
+                  const float cmj = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
+                                          ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
+                  const float scj = score(cmj, sW[r]);
+                  const bool mine = dvalid && scj <= sThr[r];
+                  if (!__any_sync(0xffffffffu, mine)) continue;
+                  bool need = mine;  // exact s: every flagged lane (no shared margin)
+                  if constexpr (MODE != MODE_EXACT) {
+                    float mn = mine ? scj : INFINITY;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                    const float lim = __fadd_ru(mn, 2.0f * sDelta[r]);
+                    need = mine && scj <= lim;
                   }
-                  const float2 d2 = __fadd2_rn(s2, make_float2(-tv[j], -tv[j + 1]));
-                  dm[j] = d2.x;
-                  dm[j + 1] = d2.y;
-                  m = ptx::fmin3(m, d2.x, d2.y);
+                  const unsigned bal = __ballot_sync(0xffffffffu, need);
+                  int64_t be = INT64_MAX, bv = 0, bk = INT64_MAX;
+                  if (need) pair_exact(v, cmj, sW[r], dr, be, bv, bk);
+                  warp_best(be, bv, bk, bal);
+                  resolve(r, be, bv, bk);
                 }
               }
             }
-            if (__any_sync(0xffffffffu, dvalid && m <= 0.f)) {
-              const DomRec dr = *drp;
-              uint32_t fl = 0;
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
+          } else {
+            // every correlation the warp needs is reduced to the 8 maxima of
+            // each half before the screen, and the accumulator goes back to
+            // the MMA at once.  In the rare case that some lane passes, of
+            // the lanes that pass a flagged range those within two margins
+            // of the warp's smallest float score can hold the range's best
+            // (usually one); they queue the pair for exact scoring (flush,
+            // which recovers the isometry of the maximum from the operands),
+            // and the range's threshold drops at once to that smallest score
+            // plus two margins -- an upper bound of the queued pair's exact
+            // score plus the margin, so a valid threshold while the pair
+            // stays queued.
+            float cmh[NH][8];
+            if (ok) {
 #pragma unroll
-              for (int j = 0; j < 8; ++j) fl |= (dvalid && dm[j] <= 0.f) ? 1u << j : 0u;
-              uint32_t wm = __reduce_or_sync(0xffffffffu, fl);
+              for (int h = 0; h < NH; ++h) {
+                uint32_t ra[32], rb[32];
+                ptx::tmem_ld64_wait(tb + (c0 + 2 * h) * 32, ra, rb);
+                max8(ra, rb, cmh[h]);
+              }
+            }
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
+            const int64_t myslot = g.slot0 + (int64_t)t * kTileDoms + dl;
+#pragma unroll
+            for (int h = 0; h < NH; ++h) {
+              const int rb0 = (c0 + 2 * h) * RPC;
+              float m = INFINITY;
+              float dm[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) dm[j] = INFINITY;
+              if (ok) screen8(cmh[h], rb0, dm, m);
+              if (__any_sync(0xffffffffu, dvalid && m <= 0.f)) {
+                uint32_t fl = 0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) fl |= (dvalid && dm[j] <= 0.f) ? 1u << j : 0u;
 #pragma unroll 1
-              for (; wm; wm &= wm - 1) {
-                const int j = __ffs(wm) - 1;
-                const int r = rb0 + j;
-                float v[8];
-                ptx::tmem_ld8_wait(tb + cb * 32 + 8 * j, v);
-                const float cmj = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
-                                        ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
-                const float scj = score(cmj, sW[r]);
-                const bool mine = dvalid && scj <= sThr[r];
-                if (!__any_sync(0xffffffffu, mine)) continue;
-                bool need = mine;  // exact s: every flagged lane (no shared margin)
-                if constexpr (MODE != MODE_EXACT) {
+                for (uint32_t wm = __reduce_or_sync(0xffffffffu, fl); wm; wm &= wm - 1) {
+                  const int j = __ffs(wm) - 1;
+                  const int r = rb0 + j;
+                  float cmj = cmh[h][0];
+#pragma unroll
+                  for (int jj = 1; jj < 8; ++jj)
+                    if (jj == j) cmj = cmh[h][jj];
+                  const float wr = sW[r];
+                  const float scj = score(cmj, wr);
+                  const bool mine = dvalid && scj <= sThr[r];
+                  if (!__any_sync(0xffffffffu, mine)) continue;
                   float mn = mine ? scj : INFINITY;
 #pragma unroll
-                  for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                  for (int o = 16; o > 0; o >>= 1)
+                    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
                   const float lim = __fadd_ru(mn, 2.0f * sDelta[r]);
-                  need = mine && scj <= lim;
+                  const bool need = mine && scj <= lim;
+                  const unsigned bal = __ballot_sync(0xffffffffu, need);
+                  const int cnt = __popc(bal);
+                  if (qn + cnt > Cf::QCAP) flush();
+                  if (need) {
+                    int pi = 0;
+                    if constexpr (MODE == MODE_GRID)
+                      pi = (int)fminf(fmaxf(rintf(fmaf(nX, wr, cmj) * F1), 0.f), qf);
+                    const int slot = qn + __popc(bal & ((1u << lane) - 1u));
+                    myq[slot] = QCand{myslot, (int32_t)cmj, r | (pi << 12)};
+                  }
+                  qn += cnt;
+                  __syncwarp();
+                  if (lane == 0 && lim < sThr[r]) {
+                    sThr[r] = lim;
+                    atomicMin(a.gthr + g.r0 + r, thr_to_ord(lim));
+                  }
+                  __syncwarp();
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, need);
-                int64_t be = INT64_MAX, bv = 0, bk = INT64_MAX;
-                if (need) pair_exact(v, cmj, sW[r], dr, be, bv, bk);
-                warp_best(be, bv, bk, bal);
-                resolve(r, be, bv, bk);
               }
             }
           }
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
         } else {
           uint32_t ra[32], rb[32];
           // two TMEM loads in flight; the accumulator goes back to the MMA
@@ -877,8 +1099,9 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(rec_empty);
       }
-      // merge the warps' bests per range; one thread per range writes the
-      // item's partial
+      // the queued candidates' exact scores, then merge the warps' bests per
+      // range; one thread per range writes the item's partial
+      flush();
       __syncwarp();
       ptx::named_bar_sync(1, epi_threads);
       if (ew == 0 && lane < kTileRanges) {
