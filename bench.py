@@ -143,9 +143,9 @@ def _sm_max_mhz():
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_match_tc
 # launch per level B on this workload, from one ncu capture of the current
-# kernel (cold caches: the operands' first touch); empty when the kernel has
-# changed since the last capture.
-TRAFFIC = {16: 20128000, 8: 6290944, 4: 3355648, 2: 3051776}
+# kernel (cold caches: the operands' first touch); absent (null) when the
+# kernel has changed since its last capture.
+TRAFFIC = {16: 20126464, 4: 3699712, 2: 3490048}
 
 
 def _dist():
