@@ -487,7 +487,8 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, uint
                              w.meta.as<PlanMeta>(), status,
                              w.res.as<fic_transform>(), prm.rms_threshold, split > 0 ? 1 : 0,
                              split >= 0 ? w.acc.as<uint8_t>() : nullptr, w.acc_cnt.as<int32_t>(),
-                             w.rej_cnt.as<int32_t>(), tile_acc, a.pm, ctx->nsm, st);
+                             w.rej_cnt.as<int32_t>(), tile_acc, a.pm,
+                             tc ? w.mom.as<RangeMom>() : nullptr, ctx->nsm, st);
 }
 
 int64_t ranges_at(const std::vector<fic_image>& ims, int B) {
@@ -876,6 +877,7 @@ int fic_match_level(fic_ctx* ctx, const fic_image* img, const fic_pool* pool,
     w.pool.bpack = src.bpack; w.pool.b32 = src.b32; w.pool.dom = src.dom;
     w.pool.domf = src.domf;
     w.pool.umax = src.umax;
+    w.pool.sd = src.sd; w.pool.sq = src.sq; w.pool.off = src.off;  // per-position sums
     std::vector<RangeRec> rec(n_ranges);
     for (int r = 0; r < n_ranges; ++r) rec[r] = RangeRec{0, range_xy[2 * r], range_xy[2 * r + 1], -1};
     const int64_t nact = n_ranges, off[2] = {0, n_ranges};
@@ -894,6 +896,7 @@ int fic_match_level(fic_ctx* ctx, const fic_image* img, const fic_pool* pool,
   w.pool.img = DevBuf(); w.pool.sel = DevBuf(); w.pool.slot_off = DevBuf();
   w.pool.bpack = DevBuf(); w.pool.b32 = DevBuf(); w.pool.dom = DevBuf(); w.pool.domf = DevBuf();
   w.pool.umax = DevBuf();
+  w.pool.sd = DevBuf(); w.pool.sq = DevBuf(); w.pool.off = DevBuf();
   if (rc) {
     fic_matches_free(m);
     return rc;

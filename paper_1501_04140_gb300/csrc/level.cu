@@ -321,14 +321,166 @@ k_reduce_final(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec
   }
 }
 
+// Tensor path: every candidate's score is exact -- E' = p^2 V - 8 p q C of
+// the predefined or grid S, or the pair's C in the exact-s mode -- so the
+// chosen map follows from exact moments already at hand: the range's A and
+// sum r (RangeMom) and the domain's sum Ds and sum Ds^2 (the pool's
+// per-position sums, V = n sum Ds^2 - (sum Ds)^2).  One thread per range, no
+// pixel reads; the same values as k_reduce_final's sums over the pixels.
+// The accept / reject counts are aggregated per warp: a warp's 32 ranges lie
+// in one kScanTile-range tile, and usually in one image.
+template <int B>
+__global__ void __launch_bounds__(256)
+k_reduce_moments(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec,
+                 const int64_t* __restrict__ n_act, const int64_t* __restrict__ act_off,
+                 int n_images, int L, const int64_t* __restrict__ item_off,
+                 const int32_t* __restrict__ chunks, const Cand* __restrict__ part, SSet S,
+                 int level, const PlanMeta* __restrict__ meta, uint32_t* __restrict__ status,
+                 const RangeMom* __restrict__ mom, fic_transform* __restrict__ res, double e_thr,
+                 int last, uint8_t* __restrict__ acc, int32_t* __restrict__ acc_cnt,
+                 int32_t* __restrict__ rej_cnt, int32_t* __restrict__ tile_acc, PosMoments pm) {
+  constexpr int n = B * B;
+  grid_dep_sync();
+  const int lane = threadIdx.x & 31;
+  const int64_t N = *n_act;
+  const bool overflow = meta->overflow != 0;
+  if (overflow && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusOverflow);
+  // (block-uniform loop: every lane of a warp takes part in its votes)
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < N;
+       g0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = g0 + threadIdx.x;
+    const bool valid = g < N;
+    int im = -1;
+    bool ok_acc = false;
+    if (valid) {
+      const RangeRec r = rec[g];
+      im = r.img;
+      const int64_t l = g - act_off[im];
+      const int64_t m = l / kTileRanges;
+      const int rr = (int)(l % kTileRanges);
+      const int nc = overflow ? 0 : chunks[im];
+      Cand best{INT64_MAX, INT64_MAX};
+      int64_t bv = 0;  // exact s: the best's V
+      for (int c = 0; c < nc; ++c) {
+        const Cand x = part[(item_off[im] + m * nc + c) * kTileRanges + rr];
+        if (S.exact) {
+          const int64_t xv = x.key == INT64_MAX ? 0 : pos_v(pm, im, x.key >> 3, n);
+          if (exact_better(x.score, xv, x.key, best.score, bv, best.key)) best = x, bv = xv;
+        } else {
+          cand_min(best, x);
+        }
+      }
+      const ImgDev I = imgs[im];
+      const bool bad = best.key == INT64_MAX || best.key < 0 ||
+                       best.key / (8 * (int64_t)S.m) >= (int64_t)I.px * I.py;
+      fic_transform t{};
+      t.level = level;
+      t.x = r.x;
+      t.y = r.y;
+      t.size = B;
+      if (!bad) {
+        const int s_idx = (int)(best.key % S.m);
+        const int iso = (int)((best.key / S.m) % 8);
+        const int pos = (int)(best.key / (8 * (int64_t)S.m));
+        const RangeMom mo = mom[g];
+        const int64_t gp = pm.off[im] + pos;
+        const int64_t sdd = pm.sd[gp], sdd2 = pm.sq[gp];
+        const int64_t sr = mo.sr, A = mo.a;
+        const int64_t V = (int64_t)n * sdd2 - sdd * sdd;
+        t.dom_index = pos;
+        t.dom_x = (pos % I.px) * L;
+        t.dom_y = (pos / I.px) * L;
+        t.iso = iso;
+        if (S.exact) {
+          // Eq. 2's s clamped to [0, 1] as sn / sd; Eq. 3's o; E in the
+          // moment form n E = A - G (double operations in this order)
+          const int64_t C = best.score;
+          int64_t sn = 0, sd = 1;
+          if (C > 0 && V > 0) {
+            if (4 * C >= V) sn = 1;
+            else sn = 4 * C, sd = V;
+          }
+          t.s_idx = 0;
+          t.p = t.q = 0;
+          t.e_num = 0;
+          t.o_num = 0;
+          t.s = __ddiv_rn((double)sn, (double)sd);
+          t.o = __ddiv_rn((double)(4 * sd * sr - sn * sdd),
+                          __dmul_rn(__dmul_rn(4.0, (double)sd), (double)n));
+          if (sn == 0)
+            t.e = __ddiv_rn((double)A, (double)n);
+          else if (sn == sd)
+            t.e = __ddiv_rn((double)(16 * A - 8 * C + V), __dmul_rn(16.0, (double)n));
+          else
+            t.e = __ddiv_rn(__dsub_rn((double)A, __ddiv_rn(__dmul_rn((double)C, (double)C), (double)V)),
+                            (double)n);
+        } else {
+          const int64_t p = S.p[s_idx], q = S.q;
+          // 16 q^2 n^2 E = n (16 q^2 A - 8 p q C + p^2 V) = n (16 q^2 A + E')
+          const int64_t enum_ = (int64_t)n * (16 * q * q * A + best.score);
+          t.s_idx = s_idx;
+          t.p = (int32_t)p;
+          t.q = (int32_t)q;
+          t.e_num = enum_;
+          t.o_num = 4 * q * sr - p * sdd;  // Eq. 3 times 4 q n
+          t.e = (double)enum_ / (16.0 * (double)(q * q) * (double)n * (double)n);
+          t.s = (double)p / (double)q;
+          t.o = (double)t.o_num / (4.0 * (double)q * (double)n);
+        }
+      } else {  // no candidate (plan overflow): flagged, never read as a map
+        t.dom_index = -1;
+        t.e = INFINITY;
+        t.e_num = INT64_MAX;
+      }
+      res[g] = t;
+      ok_acc = last || (t.e <= e_thr);  // Sec. 2: keep when acceptable, else split
+      if (acc) acc[g] = ok_acc ? 1 : 0;
+    }
+    if (acc) {
+      const unsigned am = __ballot_sync(0xffffffffu, valid && ok_acc);
+      const unsigned rm = __ballot_sync(0xffffffffu, valid && !ok_acc);
+      const int im0 = __shfl_sync(0xffffffffu, im, 0);
+      if (__all_sync(0xffffffffu, !valid || im == im0)) {
+        if (lane == 0) {
+          if (am) atomicAdd(&acc_cnt[im0], __popc(am));
+          if (rm) atomicAdd(&rej_cnt[im0], __popc(rm));
+        }
+      } else if (valid) {
+        atomicAdd(ok_acc ? &acc_cnt[im] : &rej_cnt[im], 1);
+      }
+      if (lane == 0 && am) atomicAdd(&tile_acc[(g0 + (threadIdx.x & ~31)) / kScanTile], __popc(am));
+    }
+  }
+}
+
 int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
                         int64_t cap, const int64_t* act_off, const int64_t* pool_off,
                         int n_images, int L, const SelState* sel, const int64_t* item_off,
                         const int32_t* chunks, const Cand* part, int iso_rows, const SSet& S,
                         int level, const PlanMeta* meta, uint32_t* status, fic_transform* res,
                         double rms, int last, uint8_t* acc, int32_t* acc_cnt, int32_t* rej_cnt,
-                        int32_t* tile_acc, const PosMoments& pm, int nsm, cudaStream_t st) {
+                        int32_t* tile_acc, const PosMoments& pm, const RangeMom* mom, int nsm,
+                        cudaStream_t st) {
   if (acc && !tile_acc) return FIC_EINVAL;
+  if (iso_rows == 1 && mom) {  // tensor path: from the exact moments
+    const int64_t gmax = nsm > 0 ? 8 * (int64_t)nsm : 65535;
+    const int grid = (int)std::min<int64_t>(ceil_div64(cap > 0 ? cap : 1, 256), gmax);
+    const double e_thr1 = (double)(B * B) * (rms * rms);
+    cudaError_t e;
+#define FIC_RM(BB)                                                                             \
+  launch_dep(k_reduce_moments<BB>, dim3(grid), dim3(256), 0, st, imgs, rec, n_act, act_off,    \
+             n_images, L, item_off, chunks, part, S, level, meta, status, mom, res, e_thr1,     \
+             last, acc, acc_cnt, rej_cnt, tile_acc, pm)
+    switch (B) {
+      case 16: e = FIC_RM(16); break;
+      case 8: e = FIC_RM(8); break;
+      case 4: e = FIC_RM(4); break;
+      case 2: e = FIC_RM(2); break;
+      default: return FIC_EINVAL;
+    }
+#undef FIC_RM
+    return e == cudaSuccess ? FIC_OK : FIC_ECUDA;
+  }
   const int threads = 32 * kReduceWarps;
   // grid-stride over the device count: at most 8 resident blocks per SM
   const int64_t gmax = nsm > 0 ? 8 * (int64_t)nsm : 65535;

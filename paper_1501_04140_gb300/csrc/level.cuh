@@ -87,7 +87,8 @@ int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const in
                         const int32_t* chunks, const Cand* part, int iso_rows, const SSet& S,
                         int level, const PlanMeta* meta, uint32_t* status, fic_transform* res,
                         double rms, int last, uint8_t* acc, int32_t* acc_cnt, int32_t* rej_cnt,
-                        int32_t* tile_acc, const PosMoments& pm, int nsm, cudaStream_t st);
+                        int32_t* tile_acc, const PosMoments& pm, const RangeMom* mom, int nsm,
+                        cudaStream_t st);
 
 // The saved codes and the next level's ranges of a level whose reducer took
 // the split decision (acc, the per-image counts and tile_acc, the accepted

@@ -221,17 +221,18 @@ k_pool_stats_warp16(const ImgDev* __restrict__ imgs, const int64_t* __restrict__
     const uint8_t* base = I.pix + (int64_t)(row * L) * pitch;
     int64_t key = 0;  // this lane's share of the key and moments
     int s = 0, s2 = 0;
+    // the warp's sums by hardware reductions of 32-bit values: the key as
+    // two digits key = hi 2^24 + lo (lo in [0, 2^24)); a lane's share stays
+    // below 2^41 in magnitude, so both digit sums over the 32 lanes fit
     auto emit = [&](int64_t g) {
-      int64_t k = key;
-      int a = s, b = s2;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        k += __shfl_xor_sync(0xffffffffu, k, o);
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-      }
+      const int lo = (int)(key & 0xFFFFFF);
+      const int hi = (int)(key >> 24);
+      const int slo = __reduce_add_sync(0xffffffffu, lo);
+      const int shi = __reduce_add_sync(0xffffffffu, hi);
+      const int a = __reduce_add_sync(0xffffffffu, s);
+      const int b = __reduce_add_sync(0xffffffffu, s2);
       if (lane == 0) {
-        keys[g] = k;
+        keys[g] = (int64_t)shi * (1LL << 24) + slo;
         sd[g] = a;
         sq[g] = b;
       }
