@@ -352,35 +352,52 @@ int level_alloc(fic_ctx* ctx, LevelWs& w, const std::vector<fic_image>& ims, int
   return rc ? FIC_ENOMEM : FIC_OK;
 }
 
+// The work plan of one level: its pool's kept counts and its active ranges
+// give the work items; with_split also zeroes the split counters per tile.
+PlanArgs plan_args(const fic_ctx* ctx, LevelWs& w, int items_per_cta, bool with_split) {
+  PlanArgs p{};
+  p.n_images = w.pool.n_images;
+  p.sel = w.pool.sel.as<SelState>();
+  p.target_items = items_per_cta * ctx->nsm;
+  p.item_cap = w.item_cap;
+  p.mt_cap = w.mt_cap;
+  p.meta = w.meta.as<PlanMeta>();
+  p.item_off = w.item_off.as<int64_t>();
+  p.chunks = w.chunks.as<int32_t>();
+  p.acc_cnt = w.acc_cnt.as<int32_t>();
+  p.rej_cnt = w.rej_cnt.as<int32_t>();
+  p.tile_acc = with_split ? w.scan_scr.as<int32_t>() : nullptr;
+  p.n_tiles = (int)ceil_div64(w.cap > 0 ? w.cap : 1, kScanTile);
+  return p;
+}
+
 // Matching of the active ranges of one level against the level's pool,
 // then the exact map of every range (res).
 // With split >= 0 the reducer also takes the level's split decision (split =
 // 1 on the last level, which accepts every range).  A pool built on another
 // stream joins through pool_ready, after the range operand and before the
-// plan, the first step that reads the pool.
+// plan, the first step that reads the pool.  planned: the previous level's
+// split kernel has already written this level's plan (for the level's
+// current schedule), so only a re-tune plans again here.
 int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, uint32_t* status,
                 cudaStream_t st, cudaEvent_t* ev = nullptr, int split = -1,
-                cudaEvent_t pool_ready = nullptr) {
+                cudaEvent_t pool_ready = nullptr, bool planned = false) {
   PoolLevel& pl = w.pool;
   const int ni = pl.n_images;
   const bool tc = prm.precision == FIC_PREC_TENSOR;
   const int grid = ctx->nsm;
   int32_t* tile_acc = split >= 0 ? w.scan_scr.as<int32_t>() : nullptr;
-  const int n_tiles = (int)ceil_div64(w.cap > 0 ? w.cap : 1, kScanTile);
   // range operand (also resets the ranges' shared thresholds) and the plan
-  auto pack_plan = [&](int items_per_cta) -> int {
+  auto pack_plan = [&](int items_per_cta, bool plan) -> int {
     int rc = launch_range_pack(w.B, pl.img.as<ImgDev>(), w.rec.as<RangeRec>(),
                                w.n_act.as<int64_t>(), w.cap, w.Kp, w.mom.as<RangeMom>(),
                                w.gthr.as<uint32_t>(), tc ? w.apack.as<uint16_t>() : nullptr,
                                tc ? nullptr : w.a32.as<float>(), ctx->nsm, st);
-    if (rc) return rc;
+    if (rc || !plan) return rc;
     if (pool_ready) FIC_CUDA_TRY(cudaStreamWaitEvent(st, pool_ready, 0));
-    const cudaError_t e = launch_dep(
-        k_plan, dim3(1), dim3(256), 0, st, ni, (const int64_t*)w.act_off.as<int64_t>(),
-        (const int64_t*)w.act_cnt.as<int64_t>(), (const SelState*)pl.sel.as<SelState>(),
-        items_per_cta * grid, w.item_cap, w.mt_cap, w.meta.as<PlanMeta>(),
-        w.item_off.as<int64_t>(), w.chunks.as<int32_t>(), w.acc_cnt.as<int32_t>(),
-        w.rej_cnt.as<int32_t>(), tile_acc, n_tiles);
+    const cudaError_t e =
+        launch_dep(k_plan, dim3(1), dim3(256), 0, st, plan_args(ctx, w, items_per_cta, split >= 0),
+                   (const int64_t*)w.act_off.as<int64_t>(), (const int64_t*)w.act_cnt.as<int64_t>());
     return e == cudaSuccess ? FIC_OK : FIC_ECUDA;
   };
   MatchArgs a{};
@@ -446,7 +463,7 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, uint
           // one untimed launch: a kernel's first launch carries one-time
           // costs (module loading) that would count against the candidate
           for (int t = -1; !rc && t < kTrials; ++t) {
-            if ((rc = pack_plan(cand))) break;
+            if ((rc = pack_plan(cand, true))) break;
             if (t < 0) {
               rc = match();
               continue;
@@ -472,10 +489,11 @@ int level_match(fic_ctx* ctx, LevelWs& w, const fic_params& prm, int level, uint
       w.groups_per_tile = best_groups;
       a.groups_per_tile = best_groups;
       w.tuned = true;
+      planned = false;  // the candidates overwrote the plan
     }
   }
 
-  int rc = pack_plan(w.items_per_cta);
+  int rc = pack_plan(w.items_per_cta, !planned);
   if (rc) return rc;
   if (ev) FIC_CUDA_TRY(record_event(ev[1], st));
   if ((rc = match())) return rc;
@@ -535,8 +553,9 @@ int encode_device(fic_code* c, cudaStream_t st) {
   // a fresh status for this encode (also a node of the captured graph, so
   // every replay starts clear)
   FIC_CUDA_TRY(cudaMemsetAsync(c->status.p, 0, 16, st));
-  // fork: every level's pool on its own side stream; each level joins its
-  // pool before its plan, so level 0's ranges are set up meanwhile
+  // fork: every level's pool on its own side stream; level 0 joins its pool
+  // before its plan, so level 0's ranges are set up meanwhile, and level
+  // l + 1's pool joins before level l's split, which plans level l + 1
   FIC_CUDA_TRY(cudaEventRecord(c->fork_ev, st));
   for (int l = 0; l < c->n_levels; ++l) {
     FIC_CUDA_TRY(cudaStreamWaitEvent(c->side[l], c->fork_ev, 0));
@@ -560,9 +579,15 @@ int encode_device(fic_code* c, cudaStream_t st) {
     }
     const bool last = (l == c->n_levels - 1);
     if ((rc = level_match(ctx, w, prm, l, c->status.as<uint32_t>(), st,
-                          c->profile ? c->ev[l] : nullptr, last ? 1 : 0, c->pool_ev[l])))
+                          c->profile ? c->ev[l] : nullptr, last ? 1 : 0,
+                          l == 0 ? c->pool_ev[0] : nullptr, l > 0)))
       return rc;
     LevelWs* nx = last ? nullptr : &c->lv[l + 1];
+    PlanArgs np{};
+    if (nx) {
+      FIC_CUDA_TRY(cudaStreamWaitEvent(st, c->pool_ev[l + 1], 0));
+      np = plan_args(ctx, *nx, nx->items_per_cta, true);
+    }
     rc = launch_split(w.res.as<fic_transform>(), w.rec.as<RangeRec>(), w.n_act.as<int64_t>(), w.cap,
                       w.B, ni, w.acc.as<uint8_t>(),
                       w.acc_cnt.as<int32_t>(), w.rej_cnt.as<int32_t>(), w.code_off.as<int64_t>(),
@@ -570,7 +595,7 @@ int encode_device(fic_code* c, cudaStream_t st) {
                       nx ? nx->act_off.as<int64_t>() : nullptr,
                       nx ? nx->act_cnt.as<int64_t>() : nullptr,
                       nx ? nx->n_act.as<int64_t>() : nullptr,
-                      w.scan_scr.as<int32_t>(), w.total.as<int64_t>(), st);
+                      w.scan_scr.as<int32_t>(), w.total.as<int64_t>(), nx ? &np : nullptr, st);
     if (rc) return rc;
     if (c->profile) FIC_CUDA_TRY(record_event(c->ev[l][3], st));
   }

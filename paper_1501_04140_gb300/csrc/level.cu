@@ -8,8 +8,10 @@
 //                    and Eq. 3 in exact integers for the chosen map, and the
 //                    split decision: accept when E <= n T^2 (last level:
 //                    always), otherwise four children (16 -> 8 -> 4 -> 2);
-//   k_split_scan + k_split_scatter  the saved codes and the next level's
-//                    ranges, from the reducer's accepted counts per tile.
+//   k_reduce_moments the same on the tensor path, from exact moments;
+//   k_split          the saved codes and the next level's ranges, from the
+//                    reducer's accepted counts per tile (and the next
+//                    level's plan).
 #include <math.h>
 
 #include <algorithm>
@@ -126,42 +128,43 @@ int launch_range_pack(int B, const ImgDev* imgs, const RangeRec* rec, const int6
 // ---------------------------------------------------------------- plan
 // One thread: images are few (<= kMaxImages) and this runs once per level.
 // The block also zeroes the reducer's accepted counts per compaction tile.
-__global__ void k_plan(int n_images, const int64_t* __restrict__ act_off,
-                       const int64_t* __restrict__ act_cnt, const SelState* __restrict__ sel,
-                       int target_items, int64_t item_cap, int64_t mt_cap, PlanMeta* meta,
-                       int64_t* __restrict__ item_off, int32_t* __restrict__ chunks,
-                       int32_t* __restrict__ acc_cnt, int32_t* __restrict__ rej_cnt,
-                       int32_t* __restrict__ tile_acc, int n_tiles) {
-  grid_dep_sync();
-  if (blockIdx.x != 0) return;
-  if (tile_acc)
-    for (int i = threadIdx.x; i < n_tiles; i += blockDim.x) tile_acc[i] = 0;
+// Run by one whole block (k_plan, or block 0 of the previous level's k_split).
+__device__ void plan_level(const PlanArgs& p, const int64_t* __restrict__ act_off,
+                           const int64_t* __restrict__ act_cnt) {
+  if (p.tile_acc)
+    for (int i = threadIdx.x; i < p.n_tiles; i += blockDim.x) p.tile_acc[i] = 0;
   if (threadIdx.x != 0) return;
-  // the split counters of the level start at zero (k_reduce_final adds)
-  for (int i = 0; i < n_images; ++i) acc_cnt[i] = 0, rej_cnt[i] = 0;
+  // the split counters of the level start at zero (the reduction adds)
+  for (int i = 0; i < p.n_images; ++i) p.acc_cnt[i] = 0, p.rej_cnt[i] = 0;
   int64_t work = 0;
-  for (int i = 0; i < n_images; ++i)
-    work += ceil_div64(act_cnt[i], kTileRanges) * ceil_div64(sel[i].nkept, kTileDoms);
-  int64_t ch = ceil_div64(work, target_items > 0 ? target_items : 1);
+  for (int i = 0; i < p.n_images; ++i)
+    work += ceil_div64(act_cnt[i], kTileRanges) * ceil_div64(p.sel[i].nkept, kTileDoms);
+  int64_t ch = ceil_div64(work, p.target_items > 0 ? p.target_items : 1);
   if (ch < 1) ch = 1;
-  const int64_t room = item_cap - mt_cap;
+  const int64_t room = p.item_cap - p.mt_cap;
   if (room > 0) {
     const int64_t need = ceil_div64(work, room);
     if (ch < need) ch = need;
   }
   int64_t items = 0;
-  for (int i = 0; i < n_images; ++i) {
+  for (int i = 0; i < p.n_images; ++i) {
     const int64_t mt = ceil_div64(act_cnt[i], kTileRanges);
-    const int64_t nt = ceil_div64(sel[i].nkept, kTileDoms);
+    const int64_t nt = ceil_div64(p.sel[i].nkept, kTileDoms);
     const int64_t c = nt > 0 ? ceil_div64(nt, ch) : 0;
-    item_off[i] = items;
-    chunks[i] = (int32_t)c;
+    p.item_off[i] = items;
+    p.chunks[i] = (int32_t)c;
     items += mt * c;
   }
-  item_off[n_images] = items;
-  meta->chunk_tiles = (int32_t)ch;
-  meta->items = items;
-  meta->overflow = items > item_cap ? 1 : 0;
+  p.item_off[p.n_images] = items;
+  p.meta->chunk_tiles = (int32_t)ch;
+  p.meta->items = items;
+  p.meta->overflow = items > p.item_cap ? 1 : 0;
+}
+
+__global__ void k_plan(PlanArgs p, const int64_t* __restrict__ act_off,
+                       const int64_t* __restrict__ act_cnt) {
+  grid_dep_sync();
+  if (blockIdx.x == 0) plan_level(p, act_off, act_cnt);
 }
 
 // ---------------------------------------------------------------- reduce + exact map
@@ -508,31 +511,6 @@ int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const in
 // (double) e_num / (16 q^2 n^2) against n (T T); the last level accepts
 // everything.)
 
-// One block: the per-image offsets of the codes saved at this level and of
-// the next level's ranges (4 children per split range; images stay in
-// order), and the exclusive scan of the accepted counts of the compaction
-// tiles, which gives every tile the rank of its first saved code.
-__global__ void __launch_bounds__(1024)
-k_split_scan(int n_images, const int32_t* __restrict__ acc_cnt,
-             const int32_t* __restrict__ rej_cnt, int64_t* __restrict__ code_off,
-             int64_t* __restrict__ next_off, int64_t* __restrict__ next_cnt,
-             int64_t* __restrict__ next_n, int32_t* tile_acc, int n_tiles, int64_t* total) {
-  grid_dep_sync();
-  block_scan_counts(tile_acc, n_tiles, total);
-  if (threadIdx.x != 0) return;
-  int64_t a = 0, c = 0;
-  for (int i = 0; i < n_images; ++i) {
-    code_off[i] = a;
-    if (next_off) next_off[i] = c;
-    if (next_cnt) next_cnt[i] = 4 * (int64_t)rej_cnt[i];
-    a += acc_cnt[i];
-    c += 4 * (int64_t)rej_cnt[i];
-  }
-  code_off[n_images] = a;
-  if (next_off) next_off[n_images] = c;
-  if (next_n) *next_n = c;
-}
-
 struct SplitCompact {
   const int64_t* n_act;
   const uint8_t* acc;
@@ -559,19 +537,48 @@ struct SplitCompact {
 
 // One thread per range of a kScanTile-range tile (so that the copies of
 // all the tile's ranges are in flight at once): the tile's accepted ranges
-// take consecutive code ranks from the tile's scanned count, the others four
-// children each, both in index order.
+// take consecutive code ranks from the accepted counts of the tiles before
+// it -- which the block sums itself: only the tiles that hold active ranges
+// get past the first check, so this stays small -- the others four children
+// each, both in index order.  Block 0 also writes the per-image offsets of
+// the codes saved at this level and of the next level's ranges (4 children
+// per split range; images stay in order).
 __global__ void __launch_bounds__(kScanTile)
-k_split_scatter(SplitCompact f, const int32_t* __restrict__ tile_off) {
+k_split(SplitCompact f, const int32_t* __restrict__ tile_cnt, int n_images,
+        const int32_t* __restrict__ acc_cnt, const int32_t* __restrict__ rej_cnt,
+        int64_t* __restrict__ code_off, int64_t* __restrict__ next_off,
+        int64_t* __restrict__ next_cnt, int64_t* __restrict__ next_n,
+        int64_t* __restrict__ total, PlanArgs next_plan, int plan_next) {
   __shared__ int sw[32];
   grid_dep_sync();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int64_t a = 0, c = 0;
+    for (int i = 0; i < n_images; ++i) {
+      code_off[i] = a;
+      if (next_off) next_off[i] = c;
+      if (next_cnt) next_cnt[i] = 4 * (int64_t)rej_cnt[i];
+      a += acc_cnt[i];
+      c += 4 * (int64_t)rej_cnt[i];
+    }
+    code_off[n_images] = a;
+    if (next_off) next_off[n_images] = c;
+    if (next_n) *next_n = c;
+    if (total) *total = a;
+  }
+  // the next level's work plan, from the counts just written (thread 0
+  // wrote them; the other threads only zero the next level's tile counts)
+  if (plan_next && blockIdx.x == 0) plan_level(next_plan, next_off, next_cnt);
   const int64_t n = f.size();
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   if (base >= n) return;  // uniform per block
+  int part = 0;
+  for (int t = threadIdx.x; t < (int)blockIdx.x; t += blockDim.x) part += tile_cnt[t];
+  int first = 0;
+  block_excl_scan(part, sw, &first);  // the block's sum: codes saved by the tiles before
   const int64_t i = base + threadIdx.x;
   const bool fl = i < n && f.flag(i);
   const int before = block_excl_scan(fl ? 1 : 0, sw, nullptr);
-  const int64_t r = (int64_t)tile_off[blockIdx.x] + before;
+  const int64_t r = (int64_t)first + before;
   if (i < n) f.emit(i, fl ? r : i - r, fl);
 }
 
@@ -579,14 +586,14 @@ int launch_split(const fic_transform* res, const RangeRec* rec, const int64_t* n
                  int B, int n_images, uint8_t* acc, int32_t* acc_cnt,
                  int32_t* rej_cnt, int64_t* code_off, fic_transform* codes, RangeRec* next,
                  int64_t* next_off, int64_t* next_cnt, int64_t* next_n, int32_t* tile_acc,
-                 int64_t* total, cudaStream_t st) {
+                 int64_t* total, const PlanArgs* next_plan, cudaStream_t st) {
   const int nb = (int)ceil_div64(cap > 0 ? cap : 1, kScanTile);
-  cudaError_t e = launch_dep(k_split_scan, dim3(1), dim3(1024), 0, st, n_images,
-                             (const int32_t*)acc_cnt, (const int32_t*)rej_cnt, code_off, next_off,
-                             next_cnt, next_n, tile_acc, nb, total);
-  if (e != cudaSuccess) return FIC_ECUDA;
   SplitCompact sc{n_act, acc, res, rec, codes, next, B / 2};
-  e = launch_dep(k_split_scatter, dim3(nb), dim3(kScanTile), 0, st, sc, (const int32_t*)tile_acc);
+  const PlanArgs np = next_plan ? *next_plan : PlanArgs{};
+  const cudaError_t e = launch_dep(k_split, dim3(nb), dim3(kScanTile), 0, st, sc,
+                                   (const int32_t*)tile_acc, n_images, (const int32_t*)acc_cnt,
+                                   (const int32_t*)rej_cnt, code_off, next_off, next_cnt, next_n,
+                                   total, np, next_plan && next_off && next_cnt ? 1 : 0);
   return e == cudaSuccess ? FIC_OK : FIC_ECUDA;
 }
 

@@ -76,10 +76,22 @@ __device__ inline float ord_to_thr(uint32_t u) {
   return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
 }
 
-__global__ void k_plan(int n_images, const int64_t* act_off, const int64_t* act_cnt,
-                       const SelState* sel, int target_items, int64_t item_cap, int64_t mt_cap,
-                       PlanMeta* meta, int64_t* item_off, int32_t* chunks, int32_t* acc_cnt,
-                       int32_t* rej_cnt, int32_t* tile_acc, int n_tiles);
+// A level's work plan (k_plan): work items from the device-side counts.
+struct PlanArgs {
+  int n_images;
+  const SelState* sel;    // the level's pool: n_kept per image
+  int target_items;       // work items wanted (items per CTA x CTAs)
+  int64_t item_cap, mt_cap;
+  PlanMeta* meta;
+  int64_t* item_off;      // n_images + 1
+  int32_t* chunks;        // per image
+  int32_t* acc_cnt;       // zeroed: the reduction's per-image counts
+  int32_t* rej_cnt;
+  int32_t* tile_acc;      // zeroed: accepted ranges per kScanTile tile (may be null)
+  int n_tiles;
+};
+
+__global__ void k_plan(PlanArgs p, const int64_t* act_off, const int64_t* act_cnt);
 
 int launch_reduce_final(int B, const ImgDev* imgs, const RangeRec* rec, const int64_t* n_act,
                         int64_t cap, const int64_t* act_off, const int64_t* pool_off,
@@ -97,7 +109,7 @@ int launch_split(const fic_transform* res, const RangeRec* rec, const int64_t* n
                  int B, int n_images, uint8_t* acc, int32_t* acc_cnt,
                  int32_t* rej_cnt, int64_t* code_off, fic_transform* codes, RangeRec* next,
                  int64_t* next_off, int64_t* next_cnt, int64_t* next_n, int32_t* tile_acc,
-                 int64_t* total, cudaStream_t st);
+                 int64_t* total, const PlanArgs* next_plan, cudaStream_t st);
 
 // Matchers: fill args.part for every planned item.  `grid` persistent CTAs.
 int launch_match_f32(const MatchArgs& a, int grid, cudaStream_t st);
