@@ -891,9 +891,10 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
 
         if constexpr (Cf::UNI) {
           // this warp's chunks: 8 ranges per 64-column half, one or two
-          // halves.  The float screen reduces each range's 8 correlations to
-          // their maximum and keeps each range's margin (score - threshold)
-          // in a register.
+          // halves.  Each range's 8 correlations (its isometries) come out of
+          // tensor memory already reduced to their maximum -- the reducing
+          // load of sm_103a -- and the float screen keeps each range's
+          // margin (score - threshold) in a register.
           constexpr int CPW = Cf::NCH / Cf::GPT;  // chunks per warp
           constexpr int NH = CPW / 2;             // 64-column halves
           const int c0 = CPW * cp;
@@ -933,14 +934,6 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
               }
             }
           };
-          auto max8 = [&](const uint32_t (&ra)[32], const uint32_t (&rb)[32], float (&cm)[8]) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float* v = (const float*)(j < RPC ? ra + 8 * j : rb + 8 * (j - RPC));
-              cm[j] = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
-                            ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
-            }
-          };
           if constexpr (MODE == MODE_EXACT || !Cf::DEFER) {
             // exact s, and B = 8 (where recomputing a queued pair's 8
             // correlations from the operands costs more than holding the
@@ -956,10 +949,8 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
 #pragma unroll
               for (int j = 0; j < 8; ++j) dm[j] = INFINITY;
               if (ok) {
-                uint32_t ra[32], rb[32];
-                ptx::tmem_ld64_wait(tb + cb * 32, ra, rb);
                 float cm[8];
-                max8(ra, rb, cm);
+                ptx::tmem_ldmax8x8_wait(tb + cb * 32, cm);
                 screen8(cm, rb0, dm, m);
               }
               if (__any_sync(0xffffffffu, dvalid && m <= 0.f)) {
@@ -1013,11 +1004,7 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
             float cmh[NH][8];
             if (ok) {
 #pragma unroll
-              for (int h = 0; h < NH; ++h) {
-                uint32_t ra[32], rb[32];
-                ptx::tmem_ld64_wait(tb + (c0 + 2 * h) * 32, ra, rb);
-                max8(ra, rb, cmh[h]);
-              }
+              for (int h = 0; h < NH; ++h) ptx::tmem_ldmax8x8_wait(tb + (c0 + 2 * h) * 32, cmh[h]);
             }
             ptx::tc_fence_before();
             __syncwarp();

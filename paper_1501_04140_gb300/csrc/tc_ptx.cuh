@@ -231,6 +231,29 @@ __device__ inline void tmem_ld8_wait(uint32_t taddr, float (&v)[8]) {
       : "memory");
 }
 
+// The maxima of 8 groups of 8 consecutive f32 columns (64 columns from
+// taddr) of this warp's 32 TMEM lanes: m[j] = max of columns 8j .. 8j+7.
+// Reducing loads (tcgen05.ld.red, sm_103a): the load path takes the maximum;
+// each load also returns its 8 columns, which are not used.  The wait names
+// the maxima as operands so that no use is scheduled before it.
+__device__ inline void tmem_ldmax8x8_wait(uint32_t taddr, float (&m)[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float v0, v1, v2, v3, v4, v5, v6, v7;
+    asm volatile(
+        "tcgen05.ld.red.sync.aligned.32x32b.x8.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, %8, [%9];"
+        : "=f"(v0), "=f"(v1), "=f"(v2), "=f"(v3), "=f"(v4), "=f"(v5), "=f"(v6), "=f"(v7),
+          "=f"(m[j])
+        : "r"(taddr + 8 * j)
+        : "memory");
+  }
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(m[0]), "+f"(m[1]), "+f"(m[2]), "+f"(m[3]), "+f"(m[4]), "+f"(m[5]),
+                 "+f"(m[6]), "+f"(m[7])
+               :
+               : "memory");
+}
+
 // 16 consecutive 32-bit columns of this warp's 32 TMEM lanes into r[o .. o+15].
 template <int O>
 __device__ inline void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
