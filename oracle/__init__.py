@@ -119,6 +119,8 @@ def lib():
             L.oracle_decode.argtypes = [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, _P]
             L.oracle_quantize_o.restype = None
             L.oracle_quantize_o.argtypes = [_P, C.c_int, C.c_int]
+            L.oracle_map_numerators.restype = None
+            L.oracle_map_numerators.argtypes = [_P, C.c_long, C.c_int] + [_P] * 8 + [C.c_int, _P, _P]
             L.oracle_error_num128.restype = None
             L.oracle_error_num128.argtypes = [_P, _P, C.c_int, C.c_int64, C.c_int64, _P]
             L.oracle_s_exact.restype = None
@@ -201,6 +203,21 @@ def error_num(R, Ds, p, q):
     r = np.ascontiguousarray(R, dtype=np.int64).ravel()
     d = np.ascontiguousarray(Ds, dtype=np.int64).ravel()
     return int(lib().oracle_error_num(_ptr(r), _ptr(d), r.size, p, q))
+
+
+def map_numerators(img, maps, n_threads=1):
+    """(e_num, o_num) of Eq. 1 / Eq. 3 for each map of `maps` (fields x, y,
+    size, dom_x, dom_y, iso, p, q; e.g. an encoder's output), whatever chose
+    them."""
+    a = _u8(img)
+    cols = [np.ascontiguousarray(maps[f], dtype=np.int32)
+            for f in ("x", "y", "size", "dom_x", "dom_y", "iso", "p", "q")]
+    n = len(cols[0])
+    e = np.zeros(max(n, 1), np.int64)
+    o = np.zeros(max(n, 1), np.int64)
+    lib().oracle_map_numerators(_ptr(a), a.shape[1], n, *[_ptr(c) for c in cols], n_threads,
+                                _ptr(e), _ptr(o))
+    return e[:n], o[:n]
 
 
 def error_direct(R, Ds, p, q):

@@ -224,6 +224,33 @@ int64_t oracle_error_num(const int64_t* R, const int64_t* Ds, int n, int p, int 
   return (int64_t)acc;
 }
 
+/* Eq. 1 / Eq. 3 of maps chosen elsewhere: each map on its own, with the
+ * functions above (decimation, isometry, error numerator). */
+void oracle_map_numerators(const uint8_t* img, long pitch, int n_maps, const int32_t* x,
+                           const int32_t* y, const int32_t* size, const int32_t* dom_x,
+                           const int32_t* dom_y, const int32_t* iso, const int32_t* p,
+                           const int32_t* q, int n_threads, int64_t* e_num, int64_t* o_num) {
+  if (n_threads < 1) n_threads = 1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(n_threads)
+#endif
+  for (int m = 0; m < n_maps; ++m) {
+    const int B = size[m], n = B * B;
+    int64_t R[256], Ds[256], T[256];
+    for (int i = 0; i < B; ++i)
+      for (int j = 0; j < B; ++j) R[i * B + j] = img[(long)(y[m] + i) * pitch + x[m] + j];
+    oracle_decimate(img, pitch, dom_x[m], dom_y[m], B, Ds);
+    oracle_isometry(Ds, B, iso[m], T);
+    e_num[m] = oracle_error_num(R, T, n, p[m], q[m]);
+    int64_t Sr = 0, St = 0;
+    for (int i = 0; i < n; ++i) {
+      Sr += R[i];
+      St += T[i];
+    }
+    o_num[m] = 4LL * q[m] * Sr - (int64_t)p[m] * St;
+  }
+}
+
 void oracle_error_num128(const int64_t* R, const int64_t* Ds, int n, int64_t p, int64_t q,
                          uint64_t* out) {
   int64_t Sr = 0, Sd = 0;

@@ -127,6 +127,17 @@ void oracle_match(const uint8_t* img, long pitch, int W, int H, int B, int L,
                   int n_ranges, const int32_t* s_p, int n_s, int q, int n_threads,
                   oracle_match_result* out);
 
+/* Eq. 1 and Eq. 3 of given maps, whatever chose them: map i takes the
+ * size[i] x size[i] range at (x[i], y[i]), the domain whose 2x2-sum
+ * decimation starts at (dom_x[i], dom_y[i]), isometry iso[i] and s =
+ * p[i] / q[i]; e_num[i] = 16 q^2 n^2 E (oracle_error_num on the range and the
+ * transformed decimated domain T) and o_num[i] = 4 q n o = 4 q sum R -
+ * p sum T.  The maps are independent (OpenMP over n_threads). */
+void oracle_map_numerators(const uint8_t* img, long pitch, int n_maps, const int32_t* x,
+                           const int32_t* y, const int32_t* size, const int32_t* dom_x,
+                           const int32_t* dom_y, const int32_t* iso, const int32_t* p,
+                           const int32_t* q, int n_threads, int64_t* e_num, int64_t* o_num);
+
 /* 16 q^2 n^2 E of Eq. 1 as oracle_error_num, for 64-bit p and q and as an
  * unsigned 128-bit integer (out[0] = low, out[1] = high 64 bits). */
 void oracle_error_num128(const int64_t* R, const int64_t* Ds, int n, int64_t p, int64_t q,

@@ -100,6 +100,8 @@ k_range_pack(const ImgDev* __restrict__ imgs, const RangeRec* __restrict__ rec,
       mom[g] = m;
       if (gthr) gthr[g] = kThrInit;
     }
+    // the sums are read before the next pass clears them
+    __syncthreads();
   }
 }
 

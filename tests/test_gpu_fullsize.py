@@ -67,6 +67,14 @@ def _assert_maps_equal(got, ref, fields=ALL_FIELDS):
         np.testing.assert_array_equal(got[f], ref[f], err_msg=f)
 
 
+def _assert_exact_maps(img, t):
+    """Every map's e_num and o_num are Eq. 1 / Eq. 3 at its own domain,
+    isometry and s (the oracle's arithmetic on the GPU's choices)."""
+    e, o = oracle.map_numerators(img, t, n_threads=NT)
+    bad = np.nonzero((t["e_num"] != e) | (t["o_num"] != o))[0]
+    assert bad.size == 0, (bad.size, len(t), t[bad[:4]], e[bad[:4]], o[bad[:4]])
+
+
 def _assert_stats_equal(st, rstats):
     assert len(st) == len(rstats)
     for a, b in zip(st, rstats):
@@ -221,6 +229,8 @@ def test_batch64_uneven_sizes():
     p = fic.default_params()
     code = ctx.encode([G.dev(im) for (_, _, _, im) in batch], p)
     stats = [code.stats(i) for i in range(len(batch))]
+    for i, (_, _, _, im) in enumerate(batch):
+        _assert_exact_maps(im, code.transforms(i))
 
     def pool_of(args):
         i, lv = args
@@ -250,6 +260,34 @@ def test_batch64_uneven_sizes():
     code.free()
 
 
+# ------------------------------------------------------------------ many ranges
+@pytest.mark.parametrize("B", [8, 4, 2])
+def test_match_level_more_ranges_than_one_pass(B):
+    """fic_match_level over every range of a 1024 x 1024 image (16 384,
+    65 536 and 262 144 ranges: more than the range operand kernel's blocks
+    take in one pass of their grid-stride loop): every range's exact map
+    (Eq. 1 / Eq. 3 at its chosen domain, isometry and s), and the best E of
+    sampled ranges equal the oracle's exhaustive search."""
+    fic = _fic()
+    ctx = G.ctx()
+    img = synth_image(1024, 1024, 77, n_textured=2)
+    p = fic.default_params()
+    d = G.dev(img)
+    pool = ctx.build_domain_pool(d, B, p)
+    rxy = np.array([(x, y) for y in range(0, 1024, B) for x in range(0, 1024, B)], np.int32)
+    got = ctx.match_level(d, pool, rxy, p)
+    pool.free()
+    assert len(got) == len(rxy)
+    _assert_exact_maps(img, got)
+    rng = np.random.default_rng(5 + B)
+    pick = np.sort(rng.choice(len(rxy), 24, replace=False))
+    _, kept, _, _ = oracle.pool_filter(img, B, 2, 0.5)
+    sp, q = oracle.s_set(0, 16, B)
+    ref = oracle.match(img, B, 2, kept, rxy[pick], sp, q, n_threads=NT)
+    np.testing.assert_array_equal(got["e_num"][pick], ref["e_num"])
+    np.testing.assert_array_equal(G.keys_of(got[pick], len(sp)), ref["key"])
+
+
 # ------------------------------------------------------------------ 4096 x 4096
 def test_4096_full_pool_sampled():
     """4096 x 4096 with L = 1: per level the threshold key and the kept count
@@ -265,6 +303,7 @@ def test_4096_full_pool_sampled():
     t = code.transforms(0)
     st = code.stats(0)
     code.free()
+    _assert_exact_maps(img, t)
     n_pick = {0: 6, 1: 6, 2: 16, 3: 16}
 
     def pool(lv):

@@ -224,6 +224,36 @@ def test_error_num_is_exact_eq1():
                 assert oracle.error_direct(R, Ds, p, q) == pytest.approx(float(e), rel=1e-12, abs=1e-9)
 
 
+def test_map_numerators_against_exact_eq1_eq3():
+    """oracle.map_numerators (batched Eq. 1 / Eq. 3 of given maps) against
+    exact rationals on a decimation by numpy reshape and isometries by
+    numpy.rot90 / fliplr, on maps of every size at arbitrary positions."""
+    rng = np.random.default_rng(21)
+    img = rng.integers(0, 256, size=(96, 80), dtype=np.uint8)
+    H, W = img.shape
+    rows = []
+    for _ in range(120):
+        B = int(rng.choice([2, 4, 8, 16]))
+        q = int(rng.choice([10, 15, 31]))
+        rows.append((int(rng.integers(0, W - B + 1)), int(rng.integers(0, H - B + 1)), B,
+                     int(rng.integers(0, W - 2 * B + 1)), int(rng.integers(0, H - 2 * B + 1)),
+                     int(rng.integers(0, 8)), int(rng.integers(0, q + 1)), q))
+    maps = np.array(rows, dtype=[(f, "<i4") for f in ("x", "y", "size", "dom_x", "dom_y", "iso",
+                                                      "p", "q")])
+    e_num, o_num = oracle.map_numerators(img, maps, n_threads=4)
+    for m, e, o in zip(maps, e_num, o_num):
+        x, y, B, dx, dy, k, p, q = (int(m[f]) for f in maps.dtype.names)
+        n = B * B
+        R = img[y:y + B, x:x + B].astype(np.int64)
+        Ds = img[dy:dy + 2 * B, dx:dx + 2 * B].astype(np.int64).reshape(B, 2, B, 2).sum(axis=(1, 3))
+        T = np.rot90(Ds, k=-(k % 4))
+        if k >= 4:
+            T = np.fliplr(T)
+        assert Fraction(int(e), 16 * q * q * n * n) == _eq1_fraction(R, T, Fraction(p, q))
+        assert int(o) == 4 * q * int(R.sum()) - p * int(T.sum())  # 4 q n times Eq. 3's o
+    assert oracle.map_numerators(img, maps[:0])[0].size == 0
+
+
 def test_closed_form_optimum_eq2():
     """With s = s* of Eq. 2 the error is Var_R - Cov^2 / Var_D (sum form) and
     every other s gives more."""
