@@ -1004,7 +1004,8 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
             float cmh[NH][8];
             if (ok) {
 #pragma unroll
-              for (int h = 0; h < NH; ++h) ptx::tmem_ldmax8x8_wait(tb + (c0 + 2 * h) * 32, cmh[h]);
+              for (int h = 0; h < NH; ++h)
+                ptx::tmem_ldmax8x8_wait<(NH > 1)>(tb + (c0 + 2 * h) * 32, cmh[h]);
             }
             ptx::tc_fence_before();
             __syncwarp();
