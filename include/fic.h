@@ -86,10 +86,10 @@ typedef struct {
   int grid_samples;          /* M for FIC_S_GRID                               */
   double entropy_percentile; /* threshold = pool entropy at this percentile    */
   int precision;             /* FIC_PREC_TENSOR or FIC_PREC_FP32               */
-  int autotune;              /* 0: the default schedule (4 work items per
-                                persistent CTA; on the tensor path one
-                                epilogue warp group per tile at B <= 4, two at
-                                B = 8); 1: on a level's first eager run, time
+  int autotune;              /* 0: the default schedule (3 work items per
+                                persistent CTA; on the tensor path two
+                                epilogue warp groups per tile at B <= 8);
+                                1: on a level's first eager run, time
                                 the matcher with 2, 3, 4, 6 and 8 items per
                                 CTA and, on the tensor path at B <= 8, one or
                                 two epilogue groups per tile (8 or 16 ranges

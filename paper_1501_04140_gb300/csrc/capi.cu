@@ -60,7 +60,7 @@ struct LevelWs {
   DevBuf acc_cnt, rej_cnt, code_off;
   DevBuf item_off, chunks, meta, part;
   int64_t item_cap = 0, mt_cap = 0;
-  int items_per_cta = 4;                   // the plan's work items per persistent CTA
+  int items_per_cta = 3;                   // the plan's work items per persistent CTA
   int groups_per_tile = 2;                 // tensor matcher, B <= 8: epilogue groups per tile
   bool tuned = false;                      // both chosen by timing (autotune)
   DevBuf scan_scr, total;
@@ -313,7 +313,7 @@ int level_alloc(fic_ctx* ctx, LevelWs& w, const std::vector<fic_image>& ims, int
   w.cap = cap;
   // default shape (measured on a 512 x 512 encode): one epilogue group per
   // tile (16 ranges per warp visit) at B <= 4, two at B = 8
-  w.groups_per_tile = B <= 4 ? 1 : 2;
+  w.groups_per_tile = 2;
   const int64_t C = cap + kTileRanges;  // one spare M tile
   const bool tc = prm.precision == FIC_PREC_TENSOR;
   int rc = 0;

@@ -1001,24 +1001,26 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
             // plus two margins -- an upper bound of the queued pair's exact
             // score plus the margin, so a valid threshold while the pair
             // stays queued.
-            float cmh[NH][8];
-            if (ok) {
-#pragma unroll
-              for (int h = 0; h < NH; ++h)
-                ptx::tmem_ldmax8x8_wait<(NH > 1)>(tb + (c0 + 2 * h) * 32, cmh[h]);
-            }
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
+            // With two halves per warp visit (one group per tile) the first
+            // is screened while the accumulator is still held, so that only
+            // one half's maxima are live at a time; the accumulator goes
+            // back right after the last half's loads.
             const int64_t myslot = g.slot0 + (int64_t)t * kTileDoms + dl;
 #pragma unroll
             for (int h = 0; h < NH; ++h) {
+              float cmh[8];
+              if (ok) ptx::tmem_ldmax8x8_wait(tb + (c0 + 2 * h) * 32, cmh);
+              if (h == NH - 1) {
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
+              }
               const int rb0 = (c0 + 2 * h) * RPC;
               float m = INFINITY;
               float dm[8];
 #pragma unroll
               for (int j = 0; j < 8; ++j) dm[j] = INFINITY;
-              if (ok) screen8(cmh[h], rb0, dm, m);
+              if (ok) screen8(cmh, rb0, dm, m);
               if (__any_sync(0xffffffffu, dvalid && m <= 0.f)) {
                 uint32_t fl = 0;
 #pragma unroll
@@ -1027,10 +1029,10 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
                 for (uint32_t wm = __reduce_or_sync(0xffffffffu, fl); wm; wm &= wm - 1) {
                   const int j = __ffs(wm) - 1;
                   const int r = rb0 + j;
-                  float cmj = cmh[h][0];
+                  float cmj = cmh[0];
 #pragma unroll
                   for (int jj = 1; jj < 8; ++jj)
-                    if (jj == j) cmj = cmh[h][jj];
+                    if (jj == j) cmj = cmh[jj];
                   const float wr = sW[r];
                   const float scj = score(cmj, wr);
                   const bool mine = dvalid && scj <= sThr[r];

@@ -234,11 +234,8 @@ __device__ inline void tmem_ld8_wait(uint32_t taddr, float (&v)[8]) {
 // The maxima of 8 groups of 8 consecutive f32 columns (64 columns from
 // taddr) of this warp's 32 TMEM lanes: m[j] = max of columns 8j .. 8j+7.
 // Reducing loads (tcgen05.ld.red, sm_103a): the load path takes the maximum;
-// each load also returns its 8 columns, which are not used.  The waits name
-// the maxima as operands so that no use is scheduled before them.  SERIAL:
-// one load in flight at a time (9 registers instead of 72), for callers
-// that hold other values across the loads.
-template <bool SERIAL = false>
+// each load also returns its 8 columns, which are not used.  The wait names
+// the maxima as operands so that no use is scheduled before it.
 __device__ inline void tmem_ldmax8x8_wait(uint32_t taddr, float (&m)[8]) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -249,14 +246,12 @@ __device__ inline void tmem_ldmax8x8_wait(uint32_t taddr, float (&m)[8]) {
           "=f"(m[j])
         : "r"(taddr + 8 * j)
         : "memory");
-    if constexpr (SERIAL) asm volatile("tcgen05.wait::ld.sync.aligned;" : "+f"(m[j]) : : "memory");
   }
-  if constexpr (!SERIAL)
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+f"(m[0]), "+f"(m[1]), "+f"(m[2]), "+f"(m[3]), "+f"(m[4]), "+f"(m[5]),
-                   "+f"(m[6]), "+f"(m[7])
-                 :
-                 : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(m[0]), "+f"(m[1]), "+f"(m[2]), "+f"(m[3]), "+f"(m[4]), "+f"(m[5]),
+                 "+f"(m[6]), "+f"(m[7])
+               :
+               : "memory");
 }
 
 // 16 consecutive 32-bit columns of this warp's 32 TMEM lanes into r[o .. o+15].
