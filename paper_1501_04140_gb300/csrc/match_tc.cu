@@ -5,10 +5,11 @@
 // <T_k^-1 R, D>), the correlations of a level form one dense contraction
 //     corr[domain, (range, k)] = sum_i (Ds_i - 512) (T_k^-1 R)_i ,  K = n,
 // with columns r - 128 in [-128, 127] and rows Ds - 512 in [-512, 508]: small
-// integers, exact in binary16.  Each 128-wide K slice keeps every partial sum
-// below 2^23 in magnitude (128 * 512 * 128), so the f32 accumulators of
-// tcgen05.mma kind::f16 hold the exact integer correlation; B = 16 (K = 256)
-// uses two accumulators, one per K half, added as exact integers.
+// integers, exact in binary16.  Every partial sum, in any order, is an
+// integer of magnitude at most n * 128 * 512 <= 2^24 (B = 16, K = 256), so
+// the f32 accumulator of tcgen05.mma kind::f16 holds the exact integer
+// correlation; one accumulator per tile takes the whole K (at B = 16 both
+// K-half stages).
 //
 // Orientation.  The streamed 128-domain tile is the MMA's A operand (M =
 // 128: one TMEM lane per domain) and the resident tile of 16 ranges x 8
@@ -107,7 +108,7 @@ struct TcCfg {
   using Wp = TcWarps<EG>;
   static constexpr int n = B * B;
   static constexpr int Kp = tc_kp(B);                 // K padded to the MMA K step
-  static constexpr int NKC = n > 128 ? n / 128 : 1;   // exact accumulators per tile
+  static constexpr int NKC = n > 128 ? n / 128 : 1;   // K-half stages per tile
   static constexpr int KS = Kp / NKC;                 // K per pipeline stage
   static constexpr int KSTEPS = KS / 16;              // MMAs per stage
   // B <= 8: one stage = one whole tile block (operand + scoring records),
@@ -123,10 +124,10 @@ struct TcCfg {
   static constexpr int ST_BYTES = UNI ? OP_BYTES + D_BYTES : OP_BYTES;
   static_assert(!UNI || ST_BYTES == tc_tile_bytes(B), "tile block layout");
   static constexpr int NST = B == 16 ? 4 : B == 8 ? 8 : 16;  // stages
-  static constexpr int NACC = B == 16 ? 2 : 4;                // TMEM accumulators
+  static constexpr int NACC = 4;                              // TMEM accumulators
   static constexpr int ND = UNI ? 0 : 4;                      // scoring-record stages (B = 16)
   static constexpr int TCOLS = 512;
-  static constexpr int CW = NKC == 1 ? 32 : 16;       // tile columns per epilogue chunk
+  static constexpr int CW = 32;                       // tile columns per epilogue chunk
   static constexpr int RPC = CW / 8;                  // ranges per chunk
   static constexpr int NCH = kTileRows / CW;
   // B <= 8: two groups score each tile, a warp two of its four chunks; it
@@ -159,7 +160,7 @@ struct TcCfg {
   static constexpr int BYTES = OFF_MISC + 16;
   // one CTA per SM: the CTA owns all 512 TMEM columns
   static constexpr int SMEM = BYTES < 120 * 1024 ? 120 * 1024 : BYTES;
-  static_assert(NACC * NKC * 128 <= TCOLS, "tensor memory");
+  static_assert(NACC * 128 <= TCOLS, "tensor memory");
   static_assert(BYTES + 128 <= 227 * 1024, "shared memory");
 };
 
@@ -455,7 +456,10 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
               break;
             }
             ptx::tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)((ab * Cf::NKC + kc) * kTileDoms);
+            // one accumulator per tile over the whole K (both K halves at
+            // B = 16): every partial sum is an integer of magnitude at most
+            // n * 128 * 512 <= 2^24, exact in f32
+            const uint32_t d = tmem + (uint32_t)(ab * kTileDoms);
 #pragma unroll
             for (int s = 0; s < Cf::KSTEPS; ++s) {
               const int kk = (kc * Cf::KSTEPS + s) * 2;  // core-matrix column of the range tile
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
               // resident range tile (columns = range x isometry)
               const uint64_t rd = ptx::smem_desc(sR + kk * 128, 128, 16 * Cf::Kp);
               const uint64_t dd = ptx::smem_desc(sB + st * Cf::ST_BYTES + s * 256, 128, 16 * Cf::KS);
-              ptx::mma_f16(d, dd, rd, IDESC, s > 0 ? 1u : 0u);
+              ptx::mma_f16(d, dd, rd, IDESC, (kc > 0 || s > 0) ? 1u : 0u);
             }
             if constexpr (!Cf::UNI) ptx::mma_commit(&empty_b[st]);
             ++si;
@@ -670,16 +674,9 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
         const float F0 = sX[kTileDoms + dl];
         const float F1 = sX[2 * kTileDoms + dl];
         const float F2 = MODE == MODE_EXACT ? sX[3 * kTileDoms + dl] : 0.f;
-        const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * Cf::NKC * kTileRows);
+        const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * kTileRows);
 
-        auto load = [&](int ch, uint32_t(&r)[32]) {
-          if constexpr (Cf::NKC == 1) {
-            ptx::tmem_ld32(tb + ch * 32, r);
-          } else {
-            ptx::tmem_ld16<0>(tb + ch * 16, r);
-            ptx::tmem_ld16<16>(tb + kTileRows + ch * 16, r);
-          }
-        };
+        auto load = [&](int ch, uint32_t(&r)[32]) { ptx::tmem_ld32(tb + ch * 32, r); };
 
         // exact-s mode: -(upper bound of G), see kExactErr (F0 = n^2 / V,
         // F1 = V / (4 n), F2 = V / 16)
@@ -856,19 +853,8 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
         };
         auto chunk = [&](int ch, const uint32_t* rg) {
           float c[CW];
-          if constexpr (Cf::NKC == 1) {
 #pragma unroll
-            for (int j = 0; j < CW; ++j) c[j] = __uint_as_float(rg[j]);
-          } else {  // B = 16: the two K-half accumulators, added as exact integers
-#pragma unroll
-            for (int j = 0; j < CW; j += 2) {
-              const float2 s2 =
-                  __fadd2_rn(make_float2(__uint_as_float(rg[j]), __uint_as_float(rg[j + 1])),
-                             make_float2(__uint_as_float(rg[16 + j]), __uint_as_float(rg[17 + j])));
-              c[j] = s2.x;
-              c[j + 1] = s2.y;
-            }
-          }
+          for (int j = 0; j < CW; ++j) c[j] = __uint_as_float(rg[j]);
           float wr[RPC], tr[RPC];
           if constexpr (RPC == 4) {
             const float4 wv4 = *(const float4*)(sW + 4 * ch);

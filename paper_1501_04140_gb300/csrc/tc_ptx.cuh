@@ -254,20 +254,6 @@ __device__ inline void tmem_ldmax8x8_wait(uint32_t taddr, float (&m)[8]) {
                : "memory");
 }
 
-// 16 consecutive 32-bit columns of this warp's 32 TMEM lanes into r[o .. o+15].
-template <int O>
-__device__ inline void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[O + 0]), "=r"(r[O + 1]), "=r"(r[O + 2]), "=r"(r[O + 3]), "=r"(r[O + 4]),
-        "=r"(r[O + 5]), "=r"(r[O + 6]), "=r"(r[O + 7]), "=r"(r[O + 8]), "=r"(r[O + 9]),
-        "=r"(r[O + 10]), "=r"(r[O + 11]), "=r"(r[O + 12]), "=r"(r[O + 13]), "=r"(r[O + 14]),
-        "=r"(r[O + 15])
-      : "r"(taddr)
-      : "memory");
-}
-
 // Named barrier over `count` threads (ids 1..15; 0 is __syncthreads).
 __device__ inline void named_bar_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");

@@ -169,6 +169,43 @@ def test_match_level_parity(case, prec):
         assert g["e"] == g["e_num"] / (16.0 * g["q"] * g["q"] * n * n)
 
 
+def _extreme_image(name):
+    rng = np.random.default_rng(71)
+    if name == "black":
+        return np.zeros((96, 96), np.uint8)
+    if name == "sparse_white":
+        img = np.zeros((128, 128), np.uint8)
+        img[rng.random((128, 128)) < 0.03] = 255
+        return img
+    return ((rng.random((128, 128)) < 0.5) * 255).astype(np.uint8)  # "binary"
+
+
+@pytest.mark.parametrize("name", ["black", "sparse_white", "binary"])
+@pytest.mark.parametrize("smode", [0, 1])
+def test_match_level_b16_correlations_at_the_bound(name, smode):
+    """B = 16 accumulates the whole K = 256 in one f32 accumulator: every
+    partial sum is an integer of magnitude at most 256 * 128 * 512 = 2^24.
+    Black ranges against black domains (the black image keeps every domain:
+    the entropy filter's fallback) reach exactly 2^24, sparse white pixels
+    stay just below it, random 0/255 pixels mix large terms of both signs;
+    the best E and key of every range equal the oracle's."""
+    fic = _fic()
+    img = _extreme_image(name)
+    H, W = img.shape
+    ctx = G.ctx()
+    p = fic.default_params(s_mode=smode, grid_samples=16)
+    d = G.dev(img)
+    pool = ctx.build_domain_pool(d, 16, p)
+    rxy = np.array([(x, y) for y in range(0, H, 16) for x in range(0, W, 16)], np.int32)
+    got = ctx.match_level(d, pool, rxy, p)
+    pool.free()
+    _, kept, _, _ = oracle.pool_filter(img, 16, 2, 0.5)
+    sp, q = oracle.s_set(smode, 16, 16)
+    ref = oracle.match(img, 16, 2, kept, rxy, sp, q, n_threads=8)
+    np.testing.assert_array_equal(got["e_num"], ref["e_num"])
+    np.testing.assert_array_equal(G.keys_of(got, len(sp)), ref["key"])
+
+
 ENC_CASES = [
     # (W, H, seed, textured, params)
     (96, 96, 21, 1, dict()),
