@@ -676,7 +676,11 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
         const float F2 = MODE == MODE_EXACT ? sX[3 * kTileDoms + dl] : 0.f;
         const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * kTileRows);
 
-        auto load = [&](int ch, uint32_t(&r)[32]) { ptx::tmem_ld32(tb + ch * 32, r); };
+        // B = 16: one 32-column chunk (4 ranges x 8 isometries) and each
+        // range's isometry maximum, from four reducing loads
+        auto load = [&](int ch, float (&r)[32], float (&m)[4]) {
+          ptx::tmem_ldred32(tb + ch * 32, r, m);
+        };
 
         // exact-s mode: -(upper bound of G), see kExactErr (F0 = n^2 / V,
         // F1 = V / (4 n), F2 = V / 16)
@@ -702,12 +706,10 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
           }
         };
 
-        // float screen of one (domain, range) pair: the maximum of the range's
-        // 8 isometry correlations, then the best score over S against the
+        // float screen of one (domain, range) pair from the maximum of the
+        // range's 8 isometry correlations: the best score over S against the
         // range's threshold
-        auto screen = [&](const float* v, float wr, float tr, float& cmax, float& sc) -> uint32_t {
-          cmax = fmaxf(ptx::fmax3(v[0], v[1], v[2]),
-                       ptx::fmax3(v[3], v[4], ptx::fmax3(v[5], v[6], v[7])));
+        auto screen = [&](float cmax, float wr, float tr, float& sc) -> uint32_t {
           const float y = fmaf(nX, wr, cmax);
           if constexpr (MODE == MODE_EXACT) {
             sc = exact_sc(y);
@@ -851,10 +853,7 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
             resolve(r, be, bv, bk);
           }
         };
-        auto chunk = [&](int ch, const uint32_t* rg) {
-          float c[CW];
-#pragma unroll
-          for (int j = 0; j < CW; ++j) c[j] = __uint_as_float(rg[j]);
+        auto chunk = [&](int ch, const float* c, const float* cm) {
           float wr[RPC], tr[RPC];
           if constexpr (RPC == 4) {
             const float4 wv4 = *(const float4*)(sW + 4 * ch);
@@ -867,10 +866,10 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
             wr[0] = wv2.x, wr[1] = wv2.y;
             tr[0] = tv2.x, tr[1] = tv2.y;
           }
-          float cm[RPC], scs[RPC];
+          float scs[RPC];
           uint32_t fl = 0;
 #pragma unroll
-          for (int j = 0; j < RPC; ++j) fl |= screen(c + 8 * j, wr[j], tr[j], cm[j], scs[j]) << j;
+          for (int j = 0; j < RPC; ++j) fl |= screen(cm[j], wr[j], tr[j], scs[j]) << j;
           if (!dvalid) fl = 0;
           if (__any_sync(0xffffffffu, fl != 0)) slow(c, cm, scs, wr, ch, fl);
         };
@@ -1051,25 +1050,25 @@ __global__ void __launch_bounds__(TcCfg<B, G>::Wp::THREADS, 1) k_match_tc(MatchA
             }
           }
         } else {
-          uint32_t ra[32], rb[32];
+          float ra[32], rb[32], ma[4], mb[4];
           // two TMEM loads in flight; the accumulator goes back to the MMA
           // once the tile's last chunk is in registers
-          if (ok) load(0, ra);
+          if (ok) load(0, ra, ma);
 #pragma unroll 1
           for (int ch = 0; ch < Cf::NCH; ch += 2) {
             if (ok) {
-              ptx::tmem_wait(ra);
-              load(ch + 1, rb);
-              chunk(ch, ra);
-              ptx::tmem_wait(rb);
-              if (ch + 2 < Cf::NCH) load(ch + 2, ra);
+              ptx::tmem_wait_red(ra, ma);
+              load(ch + 1, rb, mb);
+              chunk(ch, ra, ma);
+              ptx::tmem_wait_red(rb, mb);
+              if (ch + 2 < Cf::NCH) load(ch + 2, ra, ma);
             }
             if (ch + 2 >= Cf::NCH) {
               ptx::tc_fence_before();
               __syncwarp();
               if (lane == 0) ptx::mbar_arrive(&acc_empty[ab]);
             }
-            if (ok) chunk(ch + 1, rb);
+            if (ok) chunk(ch + 1, rb, mb);
           }
         }
         __syncwarp();
