@@ -16,6 +16,13 @@ the CPU oracle on the workloads the benchmark times.
 - 4096 x 4096, L = 1 (the full pool of 16.5 M positions per level): every
   level's threshold key and kept count in full and sampled maps per level
   against the oracle's exhaustive search.
+- fic_match_level over every range of a 1024 x 1024 image at B = 8, 4 and 2
+  (more ranges than one pass of the range operand kernel's grid-stride loop
+  takes), with sampled ranges against the oracle's search.
+
+In the batch, the 4096 x 4096 encode and the every-range matches, every map's
+e_num and o_num also equal the oracle's Eq. 1 / Eq. 3 at the map's own range,
+domain, isometry and s (oracle.map_numerators).
 
 Bars: integer work bit-exact (keys, thresholds, kept counts, e_num, o_num,
 tie-break keys); doubles equal (the same operations in the same order); the
